@@ -1,0 +1,345 @@
+"""Benchmark: even-odd Wilson-Dirac operator GB/s and CG time-to-1e-10.
+
+Workload (default): SU(3) fundamental fermions on a 32^3 x 64 lattice, links
+exp(i eps sum a_k T_k) with eps = 1.0 (seeded Gaussian a_k, reunitarised),
+m0 = -0.4, the Schur complement Dhat on the even sites.  One step = one
+FP32 application of Dhat (two hopping launches) on a Gaussian source, with L2
+flushed (a 256 MiB write) between steps; value = algorithmic bytes / time,
+where the bytes are the ideal-reuse model 16*l*w + 5*s*w per even site
+(l = link reals, s = spinor reals, w = bytes per real).  The same line reports
+the FP64 Dhat, the end-to-end number through the C ABI with host buffers, and
+CG on Dhat^+ Dhat to a true FP64 relative residual of 1e-10 (plain FP64,
+FP32-inner and FP16-inner mixed precision).
+
+--impl reference times the FP64 CPU oracle on the host instead (bounded
+sample: the same operator on a 16 x 8^3 lattice per step) in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Dphi GB/s (% of HBM peak) + CG time-to-1e-10, mixed/multi-RHS vs FP64"
+WORKLOAD = dict(T=64, L=32, N=3, rep="fund", eps=1.0, m0=-0.4, csw=0.0)
+SAMPLE = dict(T=16, L=8)   # bounded CPU sample for the oracle legs
+
+
+def bytes_per_even_site(N, rep, w):
+    """Ideal-reuse bytes of one Dhat application per even site: 16 l w + 5 s w."""
+    d = {"fund": N, "adj": N * N - 1, "sym": N * (N + 1) // 2, "asym": N * (N - 1) // 2}[rep]
+    l = d * d if rep == "adj" else 2 * d * d
+    s = 8 * d
+    extra = 5 * 4 if w == 2 else 0   # FP16 site scales: 5 spinor passes
+    return 16 * l * w + 5 * s * w + extra
+
+
+def flops_per_even_site(N, rep):
+    d = {"fund": N, "adj": N * N - 1, "sym": N * (N + 1) // 2, "asym": N * (N - 1) // 2}[rep]
+    hop = (64 if rep == "adj" else 128) * d * d + 56 * d
+    return 2 * hop
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------- reference arm --
+def run_reference(args):
+    """The FP64 oracle on the host: Dhat on the bounded sample lattice per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import sun
+    from oracle.dirac import Geometry, WilsonOperator
+    from paper_2405_19294_gb300 import inputs
+    wl = WORKLOAD
+    T, L = SAMPLE["T"], SAMPLE["L"]
+    g = Geometry(T, L)
+    a = inputs.algebra_coefficients(0, T, L, wl["N"])
+    U = sun.reunitarise(sun.links_from_algebra(a, wl["eps"], wl["N"]))
+    op = WilsonOperator(U, wl["N"], wl["rep"], g, wl["m0"], wl["csw"])
+    psi = inputs.gaussian_spinor(1, T, L, op.d)[0]
+    for _ in range(args.warmup):
+        op.apply_schur(psi, 0)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        op.apply_schur(psi, 0)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(t))
+    sites = g.V // 2
+    gbs = bytes_per_even_site(wl["N"], wl["rep"], 4) * sites / (ms * 1e-3) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "SU(3) fund 32^3x64 Dhat even (sampled: 16x8^3 per step)",
+                       "T": WORKLOAD["T"], "L": WORKLOAD["L"]},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"Dhat even on {T}x{L}^3 per step ({sites} even sites)"},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline_leg():
+    """Time the oracle's Dhat on the bounded sample (about 10 s of CPU work)."""
+    from oracle import sun
+    from oracle.dirac import Geometry, WilsonOperator
+    from paper_2405_19294_gb300 import inputs
+    wl = WORKLOAD
+    T, L = SAMPLE["T"], SAMPLE["L"]
+    g = Geometry(T, L)
+    a = inputs.algebra_coefficients(0, T, L, wl["N"])
+    U = sun.reunitarise(sun.links_from_algebra(a, wl["eps"], wl["N"]))
+    op = WilsonOperator(U, wl["N"], wl["rep"], g, wl["m0"], wl["csw"])
+    psi = inputs.gaussian_spinor(1, T, L, op.d)[0]
+    op.apply_schur(psi, 0)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < 10.0:
+        op.apply_schur(psi, 0)
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    gbs = bytes_per_even_site(wl["N"], wl["rep"], 4) * (g.V // 2) / dt / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)", "cores": 1,
+            "kind": "oracle", "sample": f"Dhat even on {T}x{L}^3 ({g.V // 2} even sites), {n} reps, "
+                                        f"{dt * 1e3:.1f} ms each"}
+
+
+# ------------------------------------------------------------------ main --
+def hop_source_digest():
+    h = hashlib.sha256()
+    for f in ("hop.cuh", "cplx.cuh"):
+        with open(os.path.join(ROOT, "paper_2405_19294_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per even site from the committed ncu capture, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("source_digest") != hop_source_digest():
+        return None
+    return rec.get(key)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2405_19294_gb300 import hr, inputs
+
+    wl = WORKLOAD
+    T, L, N, rep = wl["T"], wl["L"], wl["N"], wl["rep"]
+    lat = hr.Lattice(T, L, N, rep)
+    a = torch.from_numpy(inputs.algebra_coefficients(0, T, L, N)).cuda()
+    U = torch.empty((lat.V, 4, N, N, 2), dtype=torch.float64, device="cuda")
+    lat.links_from_algebra(U, a, wl["eps"], True)
+    lat.represent_links(U, True, wl["csw"])
+    del a
+    psi = inputs.gaussian_spinor(1, T, L, lat.d)
+    src_host = torch.from_numpy(np.stack([psi.real, psi.imag], -1)).pin_memory()
+    del psi
+    src = src_host.cuda()
+    stream = torch.cuda.current_stream()
+    fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
+    fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
+    for p in (hr.F64, hr.F32):
+        lat.pack(fin[p], src, hr.EVEN, p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    m0, csw = wl["m0"], wl["csw"]
+
+    def timed(prec, steps):
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.dphi(fout[prec], fin[prec], hr.EVEN, m0, csw, prec)
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return [x.elapsed_time(y) for x, y in ts]
+
+    for _ in range(args.warmup):
+        lat.dphi(fout[hr.F32], fin[hr.F32], hr.EVEN, m0, csw, hr.F32)
+    lat.synchronize()
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ms32 = timed(hr.F32, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    lat.synchronize()
+    ms_step = float(np.mean(ms32))
+    if dist:
+        tt = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    sites = lat.Vh
+    b32 = bytes_per_even_site(N, rep, 4) * sites
+    gbs = world * b32 / (ms_step * 1e-3) / 1e9
+
+    # FP64 Dhat (FP64-ALU bound on this part)
+    for _ in range(3):
+        lat.dphi(fout[hr.F64], fin[hr.F64], hr.EVEN, m0, csw, hr.F64)
+    ms64 = float(np.mean(timed(hr.F64, max(3, args.steps // 4))))
+    b64 = bytes_per_even_site(N, rep, 8) * sites
+    fl = flops_per_even_site(N, rep) * sites
+
+    # end to end through the C ABI with host buffers
+    out_host = torch.empty_like(src_host).pin_memory()
+    dev_in = torch.empty_like(src)
+    dev_out = torch.zeros_like(src)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dev_in.copy_(src_host, non_blocking=True)
+        lat.pack(fin[hr.F32], dev_in, hr.EVEN, hr.F32)
+        lat.dphi(fout[hr.F32], fin[hr.F32], hr.EVEN, m0, csw, hr.F32)
+        lat.unpack(dev_out, fout[hr.F32], hr.EVEN, hr.F32)
+        out_host.copy_(dev_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = float(np.mean(e2e_ms))
+    h2d = src_host.numel() * 8
+    d2h = out_host.numel() * 8
+
+    # CG time-to-1e-10
+    cg = None
+    if not args.no_cg:
+        cg = {}
+        fb = lat.new_field(hr.EVEN, hr.F64)
+        fx = lat.new_field(hr.EVEN, hr.F64)
+        lat.pack(fb, src, hr.EVEN, hr.F64)
+        for name, inner in (("fp64", hr.F64), ("mixed_fp32", hr.F32), ("mixed_fp16", hr.F16)):
+            res = None
+            for rep_ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = lat.cg_solve(fx, fb, hr.EVEN, m0, csw, 1e-10, inner_prec=inner, check_every=20,
+                                   raise_on_error=False)
+                res["wall_s"] = time.perf_counter() - t0
+            cg[name] = {"seconds": round(res["wall_s"], 4), "iterations": res["iterations"],
+                        "outer_steps": res["outer_steps"], "true_residual": res["true_residual"],
+                        "status": res["status"]}
+        if cg["fp64"]["seconds"] > 0:
+            for k in ("mixed_fp32", "mixed_fp16"):
+                cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[k]["seconds"], 2)
+
+    peaks, kind = measured_peaks()
+    traffic = ncu_traffic("dram_bytes_per_even_site_f32")
+    roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(gbs / world / peaks["hbm_gbs"], 4), "peak_kind": kind,
+            "traffic": (round(traffic * sites / 2) if traffic else None),
+            "kernel": "hop_kernel<3,false,1> (2 launches per Dhat)"}
+    line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "SU(3) fund 32^3x64 Dhat even (even-odd Schur), eps=1.0 reunitarised, "
+                                   "m0=-0.4", "T": T, "L": L, "N": N, "rep": rep,
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "gpu_launches": 2 * args.steps,
+            "e2e": {"value": round(world * b32 / (e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e, 3)},
+            "fp64": {"ms_per_step": round(ms64, 4), "gbs": round(b64 / (ms64 * 1e-3) / 1e9, 2),
+                     "tflops": round(fl / (ms64 * 1e-3) / 1e12, 3), "bound": "alu (FP64)"},
+            "cg": cg, "clocks": clk, "wall_timed_s": round(wall, 3)}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

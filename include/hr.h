@@ -1,0 +1,205 @@
+/*
+ * hr.h -- C ABI of libhr: the even-odd preconditioned Wilson(-clover) Dirac
+ * operator D_R for fermions in a representation R of SU(N), and conjugate
+ * gradient on the normal equations built on it, on one GB300 GPU.
+ *
+ * The paper ("GPU-accelerated Higher Representations of Wilson Fermions with
+ * HiRep") provides, on GPUs, the Wilson-Dirac operator for general higher
+ * representations of SU(N_c), single and double precision, even-odd
+ * preconditioning and clover improvement (Sec. 3.1), the spin projection to
+ * half-spinors (Sec. 2.2), site-wise linear algebra and reductions
+ * (Sec. 3.2) and the conjugate-gradient inverter (Sec. 3.3).  It prints no
+ * formula; this library implements the standard definitions:
+ *
+ *   D psi(x) = A(x) psi(x) - 1/2 sum_mu [ (1 - g_mu) U_R,mu(x) psi(x+mu)
+ *                                       + (1 + g_mu) U_R,mu(x-mu)^+ psi(x-mu) ]
+ *   A(x)     = (4 + m0) + c_sw (i/4) sum_{mu,nu} sigma_mu_nu Fhat_mu_nu(x)
+ *   Dhat_p   = A_pp - D_pq A_qq^{-1} D_qp          (p = EVEN or ODD, q = 1-p)
+ *
+ * with chiral Hermitian gammas (g_0 = [[0,-1],[-1,0]], g_k = [[0,-i s_k],
+ * [i s_k,0]], g_5 = diag(1,1,-1,-1)), periodic space, antiperiodic time (the
+ * sign sits on U_R,0 of the last time slice), parity (t+x+y+z) mod 2.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Return HR_OK (0) or a negative hr_status; nothing aborts or throws.
+ * - "device" pointers are CUDA device addresses on the current device; the
+ *   caller owns them (e.g. PyTorch tensors) and keeps them alive until the
+ *   work queued on the lattice's stream has finished.  The library owns the
+ *   represented links, the clover field and its workspaces.
+ * - Work is queued on the stream given to hr_set_stream (default: the legacy
+ *   default stream) and is asynchronous unless stated otherwise.  Kernel-side
+ *   guards latch a device error word, reported (HR_ERR_DEVICE) by the next
+ *   synchronising call.
+ * - Canonical layouts (what the caller sees), all FP64, complex as (re, im):
+ *     site index   ((t*L + z)*L + y)*L + x,  direction 0 = t, 1..3 = x, y, z
+ *     links        U[V][4][N][N]       complex, row-major
+ *     U_R          UR[V][4][d][d]      complex (imaginary part 0 for adjoint)
+ *     spinor       psi[nrhs][V][4][d]  complex (rhs, site, spin, colour)
+ *   Internal fields (hr_pack_spinor output, hr_dphi operands) are opaque
+ *   byte buffers of hr_field_bytes() bytes, 256-byte aligned.
+ */
+#ifndef HR_H
+#define HR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hr_lattice hr_lattice;
+
+typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
+/* EVEN/ODD: the Schur complement Dhat on that parity; FULL: D on the whole lattice */
+typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2 } hr_parity;
+typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2 } hr_prec;
+
+typedef enum {
+  HR_OK = 0,
+  HR_ERR_ARG = -1,           /* invalid argument (null, size, enum, csw mismatch) */
+  HR_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  HR_ERR_NOMEM = -3,         /* device allocation failed */
+  HR_ERR_STATE = -4,         /* call out of order, e.g. hr_dphi before links */
+  HR_ERR_BREAKDOWN = -5,     /* solver breakdown: <p,Ap> <= 0 or non-finite */
+  HR_ERR_NOT_CONVERGED = -6, /* solver hit maxit before the tolerance */
+  HR_ERR_UNSUPPORTED = -7,   /* combination not built (e.g. clover with d > 15) */
+  HR_ERR_DEVICE = -8         /* a kernel-side guard latched an error */
+} hr_status;
+
+typedef struct {
+  int T, L, N, rep;          /* as created */
+  int d;                     /* d_R: N, N^2-1, N(N+1)/2, N(N-1)/2 */
+  int is_real;               /* 1 for the adjoint (real links) */
+  int64_t volume;            /* V = T L^3 */
+  int64_t half_volume;       /* V/2 */
+  double flops_hop_site;     /* flops of one hopping term per output site */
+  double bytes_hop_site[3];  /* ideal-reuse bytes of one hop per output site, per hr_prec */
+} hr_info;
+
+typedef struct {
+  double tol;        /* target true relative residual |b - M x| / |b| (FP64) */
+  int maxit;         /* cap on inner iterations (all outer steps together) */
+  int inner_prec;    /* hr_prec of the inner solver; HR_F64 = plain FP64 CG */
+  double inner_tol;  /* relative residual reduction per inner solve (mixed only) */
+  int nrhs;          /* number of right-hand sides stored back to back */
+  int check_every;   /* inner iterations between residual checks on the host */
+} hr_cg_params;
+
+typedef struct {
+  int iterations;      /* inner CG iterations, summed over outer steps (max over rhs) */
+  int outer_steps;     /* FP64 residual recomputations (1 for plain FP64 CG) */
+  double true_residual;/* max over rhs of |b - M x| / |b| in FP64 at exit */
+  double seconds;      /* wall time of the call */
+  double hop_launches; /* hopping-kernel launches issued */
+} hr_cg_stats;
+
+/* ---- lattice handle --------------------------------------------------- */
+
+/* Create a T x L^3 lattice for SU(N) fermions in representation rep on the
+ * current CUDA device.  T, L even and >= 2; 2 <= N <= 6; (N=2, ASYM) is the
+ * trivial singlet and is rejected.  Allocates nothing large until links are
+ * loaded.  Errors: HR_ERR_ARG.  (Sec. 3.1: any N_c and representation.) */
+int hr_lattice_create(int T, int L, int N, int rep, hr_lattice **out);
+
+/* Free the handle and everything the library allocated for it.  Synchronises. */
+int hr_lattice_destroy(hr_lattice *lat);
+
+/* Queue all further work of this lattice on `cuda_stream` (a cudaStream_t,
+ * e.g. torch.cuda.current_stream().cuda_stream; NULL = legacy stream). */
+int hr_set_stream(hr_lattice *lat, void *cuda_stream);
+
+/* Sizes and the per-site work models. */
+int hr_lattice_info(const hr_lattice *lat, hr_info *info);
+
+/* Bytes of one internal spinor field: parity EVEN/ODD = one parity, FULL =
+ * both; `nrhs` fields back to back. */
+int hr_field_bytes(const hr_lattice *lat, int parity, int prec, int nrhs, size_t *bytes);
+
+/* Wait for the lattice's stream; report a latched device error (HR_ERR_DEVICE). */
+int hr_synchronize(hr_lattice *lat);
+
+/* ---- gauge field ------------------------------------------------------- */
+
+/* Synthetic links: U = exp(i eps sum_k a_k T_k) per link, generalised
+ * Gell-Mann T_k (tr T_a T_b = delta/2), optionally reunitarised.
+ *   a_dev : device, FP64 a[V][4][N*N-1]          (read)
+ *   U_dev : device, FP64 complex U[V][4][N][N]   (written)
+ * The exponential uses scaling and squaring of its Taylor series in FP64.
+ * (The paper generates links with its HMC, Sec. 3.4; this is the synthetic
+ * stand-in used for all benchmarks and tests.) */
+int hr_links_from_algebra(hr_lattice *lat, double *U_dev, const double *a_dev, double eps,
+                          int reunitarise);
+
+/* Load fundamental links and build the represented gauge field U_R
+ * (Sec. 3.1.2) in FP64, FP32 and FP16, with the antiperiodic-time sign.
+ *   U_dev      : device, FP64 complex U[V][4][N][N] (read only)
+ *   reunitarise: 1 = project each link onto SU(N) first (row Gram-Schmidt,
+ *                then the last row times conj(det))
+ *   csw        : clover coefficient; != 0 also builds the clover term
+ *                c_sw (i/4) sigma.Fhat from U_R (Sec. 3.1, clover) for
+ *                d <= 15, else HR_ERR_UNSUPPORTED
+ * Synchronous with respect to the lattice's stream. */
+int hr_represent_links(hr_lattice *lat, const double *U_dev, int reunitarise, double csw);
+
+/* Export U_R (with the boundary sign) in canonical FP64 complex layout
+ * UR[V][4][d][d] to device memory. */
+int hr_export_represented_links(hr_lattice *lat, double *UR_dev);
+
+/* Export the clover matrix A(x) for bare mass m0 as its two chiral blocks,
+ * canonical FP64 complex A[V][2][2d][2d] (block 0 acts on spins 0,1, block 1
+ * on spins 2,3; index spin_in_block*d + colour).  inverse = 1 exports
+ * A(x)^{-1} instead.  Needs csw != 0 at hr_represent_links. */
+int hr_export_clover(hr_lattice *lat, double *A_dev, double m0, int inverse);
+
+/* ---- spinor fields ------------------------------------------------------ */
+
+/* Canonical FP64 spinors psi[nrhs][V][4][d] (device) -> internal field of
+ * the given parity and precision (device).  Only sites of that parity are
+ * read (both for FULL).  FP16 code: per site, scale = max |fp32(v)| over its
+ * 8d reals, stored values fp16_rn(fp32(v) / scale) with IEEE division. */
+int hr_pack_spinor(hr_lattice *lat, void *internal, const double *canonical, int parity,
+                   int prec, int nrhs);
+
+/* Internal field -> canonical FP64 spinors (device).  Sites of the other
+ * parity are left untouched (set to zero first if that matters). */
+int hr_unpack_spinor(hr_lattice *lat, double *canonical, const void *internal, int parity,
+                     int prec, int nrhs);
+
+/* ---- operator ------------------------------------------------------------ */
+
+/* out = Dhat_p in (parity EVEN/ODD) or D in (FULL), or the adjoint with
+ * dagger = 1 (= g5 D g5), on `nrhs` internal fields of precision prec.
+ * FP64 fields compute in FP64; FP32 and FP16 fields accumulate in FP32.
+ * csw must equal the value given to hr_represent_links.  `in` and `out`
+ * must not overlap.  Two hopping launches, no host synchronisation. */
+int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,
+            int prec, int nrhs, int dagger);
+
+/* ---- linear algebra (Sec. 3.2) ------------------------------------------ */
+
+/* Global sums over internal fields, FP64 accumulation, deterministic order.
+ * Result written to host memory; synchronises the stream. */
+int hr_norm2(hr_lattice *lat, const void *x, int parity, int prec, int nrhs,
+             double *out_host);
+
+/* ---- solver (Sec. 3.3) ----------------------------------------------------- */
+
+/* Solve (Dhat_p^+ Dhat_p) x = b (parity EVEN/ODD) or (D^+ D) x = b (FULL)
+ * for nrhs FP64 internal fields, to a true FP64 relative residual
+ * params->tol per rhs.  inner_prec = HR_F64: plain CG.  HR_F32 / HR_F16:
+ * the inner CG runs in that precision (FP32 accumulation) and an FP64
+ * defect-correction loop recomputes b - M x in FP64 until params->tol.
+ * x is overwritten (initial guess ignored: x0 = 0).  Synchronous.
+ * Errors: HR_ERR_NOT_CONVERGED (stats still filled), HR_ERR_BREAKDOWN. */
+int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
+                const hr_cg_params *params, hr_cg_stats *stats);
+
+/* Human-readable text of an hr_status. */
+const char *hr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HR_H */

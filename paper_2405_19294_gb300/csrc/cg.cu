@@ -1,0 +1,380 @@
+// Conjugate gradient on the normal equations (Sec. 3.3), plain FP64 or mixed
+// precision, for one or many right-hand sides at once.
+//
+// One CG iteration is seven launches with no host round trip:
+//   t = Dhat p, Ap = Dhat^+ t           (4 hopping launches)
+//   pAp = |t|^2, alpha = rr / pAp       (reduction; scalars stay on the GPU)
+//   x += alpha p, r -= alpha Ap, rr'    (fused update + reduction, beta = rr'/rr)
+//   p = r + beta p
+// A chunk of `check_every` iterations is captured once into a CUDA graph and
+// replayed; after each chunk the host reads |r|^2 per right-hand side.  A
+// right-hand side whose recursive residual reached its stop value is frozen
+// on the device (alpha = 0) while the others continue.
+//
+// Mixed precision is defect correction: the FP64 residual r = b - M x is
+// rescaled to unit norm, the inner CG (FP32, or FP16 operator fields with
+// per-site scales and FP32 x, r) reduces it by inner_tol, x += |r| e in FP64,
+// and r is recomputed exactly in FP64, until |r| <= tol |b|.
+#include <chrono>
+#include <math.h>
+#include <string.h>
+
+#include "blas.cuh"
+#include "hr_internal.h"
+
+struct hr_cg_work {
+  size_t cap[3];        // bytes per buffer set, per precision
+  void *f[3][5];        // per precision: r, p, Ap, t, x(low)
+  double *scal;         // device scalars: [NS][HR_MAX_RHS]
+  double *host;         // pinned mirror
+  int *iters;           // [HR_MAX_RHS]
+  cudaStream_t s;
+};
+
+enum { S_RR0 = 0, S_RR1, S_PAP, S_ALPHA, S_BETA, S_STOP, S_A, S_B, S_OUT, NS };
+
+void hr_cg_free(hr_lattice *lat) {
+  hr_cg_work *w = lat->cg;
+  if (!w) return;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 5; ++q) cudaFree(w->f[p][q]);
+  cudaFree(w->scal);
+  cudaFree(w->iters);
+  cudaFreeHost(w->host);
+  if (w->s) cudaStreamDestroy(w->s);
+  delete w;
+  lat->cg = nullptr;
+}
+
+static int cg_work(hr_lattice *lat, int prec, size_t bytes) {
+  if (!lat->cg) {
+    hr_cg_work *w = new hr_cg_work;
+    memset(w, 0, sizeof(*w));
+    lat->cg = w;
+    HR_CUDA(cudaMalloc(&w->scal, sizeof(double) * NS * HR_MAX_RHS));
+    HR_CUDA(cudaMemset(w->scal, 0, sizeof(double) * NS * HR_MAX_RHS));
+    HR_CUDA(cudaMalloc(&w->iters, sizeof(int) * HR_MAX_RHS));
+    HR_CUDA(cudaMallocHost(&w->host, sizeof(double) * NS * HR_MAX_RHS));
+    HR_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
+  }
+  hr_cg_work *w = lat->cg;
+  if (w->cap[prec] < bytes) {
+    for (int q = 0; q < 5; ++q) {
+      cudaFree(w->f[prec][q]);
+      w->f[prec][q] = nullptr;
+    }
+    w->cap[prec] = 0;
+    for (int q = 0; q < 5; ++q) HR_CUDA(cudaMalloc(&w->f[prec][q], bytes));
+    w->cap[prec] = bytes;
+  }
+  return HR_OK;
+}
+
+static double *S(hr_cg_work *w, int k) { return w->scal + (size_t)k * HR_MAX_RHS; }
+
+struct CgCtx {
+  hr_lattice *lat;
+  int parity, nrhs, dagger_unused;
+  double m0, csw;
+  cudaStream_t s;
+  RedArgs red;
+};
+
+// Ap = M p = Dhat^+ Dhat p through t; fused |t|^2 -> pAp and alpha
+static int apply_normal(CgCtx &c, int prec, void *Ap, const void *p, void *t, const FieldDesc &f, int finish,
+                        const double *rr) {
+  HR_TRY(hr_dphi_impl(c.lat, t, p, c.parity, c.m0, c.csw, prec, c.nrhs, 0, c.s));
+  RedArgs red = c.red;
+  red.out = S(c.lat->cg, S_PAP);
+  red.rr = rr;
+  red.alpha = S(c.lat->cg, S_ALPHA);
+  if (finish != RED_NONE_SKIP) HR_TRY(hr_blas_norm2(f, prec, t, c.nrhs, red, finish, c.s));
+  HR_TRY(hr_dphi_impl(c.lat, Ap, t, c.parity, c.m0, c.csw, prec, c.nrhs, 1, c.s));
+  return HR_OK;
+}
+
+// one CG iteration on fields (x, r: prec pr; p, Ap, t: prec pp); rr buffers alternate
+static int cg_iteration(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap, void *t, const FieldDesc &fr,
+                        const FieldDesc &fp, int odd) {
+  hr_cg_work *w = c.lat->cg;
+  double *rr = S(w, odd ? S_RR1 : S_RR0);
+  double *rr_next = S(w, odd ? S_RR0 : S_RR1);
+  HR_TRY(apply_normal(c, pp, Ap, p, t, fp, RED_ALPHA, rr));
+  RedArgs red = c.red;
+  red.out = S(w, S_OUT);
+  red.rr = rr;
+  red.rr_next = rr_next;
+  red.alpha = S(w, S_ALPHA);
+  red.beta = S(w, S_BETA);
+  HR_TRY(hr_blas_cg_xr(pr, pp, x, r, p, Ap, fr, fp, c.nrhs, red, c.s));
+  HR_TRY(hr_blas_cg_p(pr, pp, r, p, fr, fp, c.nrhs, S(w, S_BETA), S(w, S_ALPHA), c.s));
+  return HR_OK;
+}
+
+// Run CG iterations until every rhs is frozen (rr <= stop) or maxit.  Fields
+// must be initialised: r, p = r, x = 0, rr in S_RR0, stop in S_STOP.
+static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap, void *t, const FieldDesc &fr,
+                   const FieldDesc &fp, int check_every, int maxit, int *iters_done) {
+  hr_cg_work *w = c.lat->cg;
+  if (check_every < 2) check_every = 2;
+  check_every &= ~1;  // even: the rr double buffer returns to S_RR0
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double hops_before = c.lat->hop_launches;  // capture records launches, replays run them
+  HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+  int rc = HR_OK;
+  for (int k = 0; k < check_every && rc == HR_OK; ++k) rc = cg_iteration(c, pr, pp, x, r, p, Ap, t, fr, fp, k & 1);
+  cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
+  const double hops_per_replay = c.lat->hop_launches - hops_before;
+  c.lat->hop_launches = hops_before;
+  if (rc != HR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  HR_CUDA(ce);
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  HR_CUDA(ce);
+  int done = 0;
+  int status = HR_OK;
+  while (done < maxit) {
+    ce = cudaGraphLaunch(exec, c.s);
+    if (ce != cudaSuccess) break;
+    c.lat->hop_launches += hops_per_replay;
+    done += check_every;
+    ce = cudaMemcpyAsync(w->host, w->scal, sizeof(double) * NS * HR_MAX_RHS, cudaMemcpyDeviceToHost, c.s);
+    if (ce != cudaSuccess) break;
+    ce = cudaStreamSynchronize(c.s);
+    if (ce != cudaSuccess) break;
+    bool all = true;
+    for (int q = 0; q < c.nrhs; ++q) {
+      const double rrq = w->host[S_RR0 * HR_MAX_RHS + q];
+      if (!(rrq <= w->host[S_STOP * HR_MAX_RHS + q])) all = false;
+      if (!isfinite(rrq)) {
+        status = HR_ERR_BREAKDOWN;
+        all = true;
+      }
+    }
+    if (all) break;
+  }
+  cudaGraphExecDestroy(exec);
+  if (ce != cudaSuccess) {
+    hr_note_cuda_error(ce, "cg_loop", __FILE__, __LINE__);
+    return HR_ERR_CUDA;
+  }
+  int err = 0;
+  HR_CUDA(cudaMemcpy(&err, c.lat->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    HR_CUDA(cudaMemset(c.lat->dev_err, 0, sizeof(int)));
+    status = HR_ERR_BREAKDOWN;
+  }
+  *iters_done = done;
+  return status;
+}
+
+// r = b - M x (FP64), returns |r|^2 per rhs on the host (w->host S_OUT)
+static int true_residual(CgCtx &c, void *r, const void *b, const void *x, void *Ap, void *t, const FieldDesc &f,
+                         double *rn2) {
+  hr_cg_work *w = c.lat->cg;
+  HR_TRY(apply_normal(c, HR_F64, Ap, x, t, f, RED_NONE_SKIP, nullptr));
+  double one[HR_MAX_RHS], zero[HR_MAX_RHS], mone[HR_MAX_RHS];
+  for (int q = 0; q < HR_MAX_RHS; ++q) {
+    one[q] = 1.0;
+    zero[q] = 0.0;
+    mone[q] = -1.0;
+  }
+  HR_CUDA(cudaMemcpyAsync(S(w, S_A), one, sizeof(one), cudaMemcpyHostToDevice, c.s));
+  HR_CUDA(cudaMemcpyAsync(S(w, S_B), zero, sizeof(zero), cudaMemcpyHostToDevice, c.s));
+  RedArgs red = c.red;
+  red.out = S(w, S_OUT);
+  HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+  HR_CUDA(cudaMemcpyAsync(S(w, S_A), mone, sizeof(mone), cudaMemcpyHostToDevice, c.s));
+  HR_CUDA(cudaMemcpyAsync(S(w, S_B), one, sizeof(one), cudaMemcpyHostToDevice, c.s));
+  HR_TRY(hr_blas_axpby(HR_F64, HR_F64, Ap, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
+  HR_CUDA(cudaMemcpyAsync(rn2, S(w, S_OUT), sizeof(double) * c.nrhs, cudaMemcpyDeviceToHost, c.s));
+  HR_CUDA(cudaStreamSynchronize(c.s));
+  return HR_OK;
+}
+
+static int set_scalars(CgCtx &c, int which, const double *v) {
+  HR_CUDA(cudaMemcpyAsync(S(c.lat->cg, which), v, sizeof(double) * c.nrhs, cudaMemcpyHostToDevice, c.s));
+  return HR_OK;
+}
+
+extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
+                           const hr_cg_params *prm, hr_cg_stats *st) {
+  if (!lat || !x || !b || !prm || parity < HR_EVEN || parity > HR_FULL) return HR_ERR_ARG;
+  if (!lat->have_links) return HR_ERR_STATE;
+  if (csw != lat->csw) return HR_ERR_ARG;
+  const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;
+  if (nrhs > HR_MAX_RHS || prm->tol <= 0.0 || prm->inner_prec < HR_F64 || prm->inner_prec > HR_F16)
+    return HR_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  const double hop0 = lat->hop_launches;
+  const int nsub = parity == HR_FULL ? 2 : 1;
+  const int lo = prm->inner_prec;
+  const size_t fb64 = hr_spinor_field_bytes(lat->Vh, lat->d, HR_F64);
+  HR_TRY(cg_work(lat, HR_F64, fb64 * nsub * nrhs));
+  if (lo != HR_F64) {
+    HR_TRY(cg_work(lat, HR_F32, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F32) * nsub * nrhs));
+    if (lo == HR_F16) HR_TRY(cg_work(lat, HR_F16, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F16) * nsub * nrhs));
+  }
+  HR_TRY(hr_red_scratch(lat, nrhs));
+  if (csw != 0.0) HR_TRY(hr_clover_prepare(lat, m0));
+  hr_cg_work *w = lat->cg;
+  // the Schur intermediate must exist before graph capture
+  if (parity != HR_FULL) {
+    size_t mx = fb64;
+    HR_TRY(hr_ensure_tmp(lat, mx * nrhs));
+  }
+  CgCtx c;
+  memset(&c, 0, sizeof(c));
+  c.lat = lat;
+  c.parity = parity;
+  c.nrhs = nrhs;
+  c.m0 = m0;
+  c.csw = csw;
+  c.s = w->s;
+  c.red.partials = lat->red_partials;
+  c.red.count = lat->red_count;
+  c.red.err = lat->dev_err;
+  c.red.stop = S(w, S_STOP);
+  c.red.iters = w->iters;
+  // order after the caller's stream
+  cudaEvent_t ev;
+  HR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HR_CUDA(cudaEventRecord(ev, lat->stream));
+  HR_CUDA(cudaStreamWaitEvent(c.s, ev, 0));
+  HR_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * HR_MAX_RHS, c.s));
+
+  FieldDesc f64;
+  f64.Vh = lat->Vh;
+  f64.d = lat->d;
+  f64.fb = fb64;
+  f64.nsub = nsub;
+  const size_t bytes64 = fb64 * nsub * nrhs;
+  void *r = w->f[HR_F64][0], *p = w->f[HR_F64][1], *Ap = w->f[HR_F64][2], *t = w->f[HR_F64][3];
+
+  double bn2[HR_MAX_RHS], rn2[HR_MAX_RHS], v[HR_MAX_RHS];
+  int status = HR_OK, iters = 0, outer = 0;
+  const int check_every = prm->check_every > 0 ? prm->check_every : 10;
+  const int maxit = prm->maxit > 0 ? prm->maxit : 100000;
+  // x = 0, r = b, |b|^2
+  HR_CUDA(cudaMemsetAsync(x, 0, bytes64, c.s));
+  {
+    double one[HR_MAX_RHS], zero[HR_MAX_RHS];
+    for (int q = 0; q < HR_MAX_RHS; ++q) {
+      one[q] = 1.0;
+      zero[q] = 0.0;
+    }
+    HR_TRY(set_scalars(c, S_A, one));
+    HR_TRY(set_scalars(c, S_B, zero));
+    RedArgs red = c.red;
+    red.out = S(w, S_OUT);
+    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, r, f64, f64, nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
+    HR_CUDA(cudaMemcpyAsync(bn2, S(w, S_OUT), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c.s));
+    HR_CUDA(cudaStreamSynchronize(c.s));
+  }
+  for (int q = 0; q < nrhs; ++q) rn2[q] = bn2[q];
+
+  if (lo == HR_F64) {
+    // ---------------------------------------------------------- plain FP64
+    HR_CUDA(cudaMemcpyAsync(p, r, bytes64, cudaMemcpyDeviceToDevice, c.s));
+    for (int q = 0; q < nrhs; ++q) v[q] = prm->tol * prm->tol * bn2[q];
+    HR_TRY(set_scalars(c, S_STOP, v));
+    while (true) {
+      HR_TRY(set_scalars(c, S_RR0, rn2));
+      int done = 0;
+      status = cg_loop(c, HR_F64, HR_F64, x, r, p, Ap, t, f64, f64, check_every, maxit - iters, &done);
+      iters += done;
+      ++outer;
+      if (status != HR_OK) break;
+      HR_TRY(true_residual(c, r, b, x, Ap, t, f64, rn2));
+      bool ok = true;
+      for (int q = 0; q < nrhs; ++q)
+        if (!(rn2[q] <= prm->tol * prm->tol * bn2[q])) ok = false;
+      if (ok) break;
+      if (iters >= maxit) {
+        status = HR_ERR_NOT_CONVERGED;
+        break;
+      }
+      // restart from the true residual
+      HR_CUDA(cudaMemcpyAsync(p, r, bytes64, cudaMemcpyDeviceToDevice, c.s));
+    }
+  } else {
+    // ------------------------------------------------- mixed precision
+    const size_t fb32 = hr_spinor_field_bytes(lat->Vh, lat->d, HR_F32);
+    const size_t fblo = hr_spinor_field_bytes(lat->Vh, lat->d, lo);
+    FieldDesc f32, flo;
+    f32 = f64;
+    f32.fb = fb32;
+    flo = f64;
+    flo.fb = fblo;
+    void *xl = w->f[HR_F32][4], *rl = w->f[HR_F32][0];
+    void *pl = w->f[lo][1], *Apl = w->f[lo][2], *tl = w->f[lo][3];
+    const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 1e-2);
+    const int maxouter = 200;
+    while (true) {
+      bool ok = true;
+      for (int q = 0; q < nrhs; ++q)
+        if (!(rn2[q] <= prm->tol * prm->tol * bn2[q])) ok = false;
+      if (ok) break;
+      if (iters >= maxit || outer >= maxouter) {
+        status = HR_ERR_NOT_CONVERGED;
+        break;
+      }
+      // rl = r / |r|, pl = rl, xl = 0; stop = (max(inner_tol, tol |b| / (2 |r|)))^2
+      double a[HR_MAX_RHS], zero[HR_MAX_RHS], one[HR_MAX_RHS], stop[HR_MAX_RHS], rr[HR_MAX_RHS];
+      for (int q = 0; q < nrhs; ++q) {
+        const double rn = sqrt(rn2[q]);
+        a[q] = rn > 0.0 ? 1.0 / rn : 0.0;
+        zero[q] = 0.0;
+        one[q] = 1.0;
+        double red_target = prm->tol * sqrt(bn2[q]) / (2.0 * (rn > 0.0 ? rn : 1.0));
+        if (red_target < inner_tol) red_target = inner_tol;
+        stop[q] = rn > 0.0 ? red_target * red_target : 1e300;
+        rr[q] = rn > 0.0 ? 1.0 : 0.0;
+      }
+      HR_TRY(set_scalars(c, S_A, a));
+      HR_TRY(set_scalars(c, S_B, zero));
+      RedArgs red = c.red;
+      red.out = S(w, S_OUT);
+      HR_TRY(hr_blas_axpby(HR_F64, HR_F32, r, rl, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_TRY(set_scalars(c, S_A, one));
+      HR_TRY(hr_blas_axpby(HR_F32, lo, rl, pl, f32, flo, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_CUDA(cudaMemsetAsync(xl, 0, fb32 * nsub * nrhs, c.s));
+      HR_TRY(set_scalars(c, S_STOP, stop));
+      HR_TRY(set_scalars(c, S_RR0, rr));
+      int done = 0;
+      status = cg_loop(c, HR_F32, lo, xl, rl, pl, Apl, tl, f32, flo, check_every, maxit - iters, &done);
+      iters += done;
+      ++outer;
+      if (status != HR_OK) break;
+      // x += |r| xl
+      for (int q = 0; q < nrhs; ++q) a[q] = sqrt(rn2[q]);
+      HR_TRY(set_scalars(c, S_A, a));
+      HR_TRY(set_scalars(c, S_B, one));
+      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, xl, x, f32, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_TRY(true_residual(c, r, b, x, Ap, t, f64, rn2));
+    }
+  }
+  HR_CUDA(cudaStreamSynchronize(c.s));
+  HR_CUDA(cudaEventDestroy(ev));
+  if (st) {
+    int it[HR_MAX_RHS];
+    HR_CUDA(cudaMemcpy(it, w->iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
+    int mx = 0;
+    double res = 0.0;
+    for (int q = 0; q < nrhs; ++q) {
+      if (it[q] > mx) mx = it[q];
+      const double rq = bn2[q] > 0.0 ? sqrt(rn2[q] / bn2[q]) : 0.0;
+      if (rq > res) res = rq;
+    }
+    st->iterations = mx;
+    st->outer_steps = outer;
+    st->true_residual = res;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    st->hop_launches = lat->hop_launches - hop0;
+  }
+  return status;
+}

@@ -1,0 +1,330 @@
+// The spin-projected 8-neighbour hopping kernel (one output site per thread).
+//
+// For output parity p and each output site x it computes
+//   H(x) = sum_mu [ (1 - s g_mu) U_R,mu(x) psi(x+mu) + (1 + s g_mu) U_R,mu(x-mu)^+ psi(x-mu) ]
+// (s = +1 for D, -1 for D^+ = g5 D g5) and applies the epilogue
+//   HOP_SCALED:  out = coef * H            or  A^{-1} (coef * H)   (clover)
+//   HOP_SELF  :  out = diag * self + coef*H or  A self + coef * H   (clover)
+// which covers the two halves of the Schur complement and the full operator
+// (Sec. 3.1, even-odd preconditioning and clover).
+//
+// Each neighbour spinor is projected to a half-spinor (two spin rows) before
+// the colour multiply, the projection of Sec. 2.2, so each U_R (or U_R^+)
+// multiplies 2 instead of 4 colour vectors; the two lower spin rows are
+// rebuilt from the products.  With the chiral gammas and projector
+// (1 + sig g_mu):
+//   mu=0: h0 = p0 - sig p2,    h1 = p1 - sig p3;    row2 = -sig r0,   row3 = -sig r1
+//   mu=1: h0 = p0 - i sig p3,  h1 = p1 - i sig p2;  row2 = i sig r1,  row3 = i sig r0
+//   mu=2: h0 = p0 - sig p3,    h1 = p1 + sig p2;    row2 = sig r1,    row3 = -sig r0
+//   mu=3: h0 = p0 - i sig p2,  h1 = p1 + i sig p3;  row2 = i sig r0,  row3 = -i sig r1
+// where r0, r1 are the colour products of h0, h1.  The sign sig is a runtime
+// +-1 so D and D^+ share one kernel (the adds become FMAs with +-1).
+#pragma once
+
+#include "cplx.cuh"
+#include "hr_internal.h"
+
+struct HopK {
+  void *out;
+  const void *in;
+  const void *self;
+  const void *links;
+  const void *clover;
+  int T, L, Lh, p, mode, nch;
+  int64_t Vh;
+  size_t stride;
+  double sgn, coef, diag;
+};
+
+template <int MU, typename R>
+__device__ __forceinline__ void project(R sig, const cx<R> psi[4], cx<R> &h0, cx<R> &h1) {
+  if (MU == 0) {
+    h0 = axpy_r(-sig, psi[2], psi[0]);
+    h1 = axpy_r(-sig, psi[3], psi[1]);
+  } else if (MU == 1) {
+    h0 = axpy_i(-sig, psi[3], psi[0]);
+    h1 = axpy_i(-sig, psi[2], psi[1]);
+  } else if (MU == 2) {
+    h0 = axpy_r(-sig, psi[3], psi[0]);
+    h1 = axpy_r(sig, psi[2], psi[1]);
+  } else {
+    h0 = axpy_i(-sig, psi[2], psi[0]);
+    h1 = axpy_i(sig, psi[3], psi[1]);
+  }
+}
+
+template <int MU, typename R>
+__device__ __forceinline__ void reconstruct(R sig, cx<R> r0, cx<R> r1, cx<R> acc[4]) {
+  acc[0] = acc[0] + r0;
+  acc[1] = acc[1] + r1;
+  if (MU == 0) {
+    acc[2] = axpy_r(-sig, r0, acc[2]);
+    acc[3] = axpy_r(-sig, r1, acc[3]);
+  } else if (MU == 1) {
+    acc[2] = axpy_i(sig, r1, acc[2]);
+    acc[3] = axpy_i(sig, r0, acc[3]);
+  } else if (MU == 2) {
+    acc[2] = axpy_r(sig, r1, acc[2]);
+    acc[3] = axpy_r(-sig, r0, acc[3]);
+  } else {
+    acc[2] = axpy_i(sig, r0, acc[2]);
+    acc[3] = axpy_i(-sig, r1, acc[3]);
+  }
+}
+
+// One direction, one side: project psi(j), multiply by U (or U^+ when ADJ),
+// accumulate.  `lk` points at chunk 0 of the link slot, `li` is the link's
+// site index in that slot.
+template <int D, bool REAL, int P, int MU, bool ADJ>
+__device__ __forceinline__ void hop_dir(cx<typename PT<P>::A> acc[D][4], const void *in, int64_t Vh,
+                                        int64_t j, const void *lk, int64_t li,
+                                        typename PT<P>::A sig, typename PT<P>::A scl) {
+  typedef typename PT<P>::A A;
+  cx<A> h0[D], h1[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    cx<A> psi[4];
+    ld_colour<P>(in, Vh, j, c, psi);
+    project<MU>(sig, psi, h0[c], h1[c]);
+    if (P == 2) {
+      h0[c] = scale(scl, h0[c]);
+      h1[c] = scale(scl, h1[c]);
+    }
+  }
+  if (REAL) {
+    constexpr int NC = (D * D + 1) / 2;
+    cx<A> u[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) u[k] = ld2<P>(lk, (int64_t)k * Vh + li);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      cx<A> r0 = mk(A(0), A(0)), r1 = mk(A(0), A(0));
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const int e = ADJ ? (c * D + a) : (a * D + c);
+        const A ue = (e & 1) ? u[e >> 1].y : u[e >> 1].x;
+        r0 = rfma(ue, h0[c], r0);
+        r1 = rfma(ue, h1[c], r1);
+      }
+      reconstruct<MU>(sig, r0, r1, acc[a]);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      cx<A> r0 = mk(A(0), A(0)), r1 = mk(A(0), A(0));
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (ADJ) {
+          const cx<A> ue = ld2<P>(lk, (int64_t)(c * D + a) * Vh + li);
+          r0 = cfmac(ue, h0[c], r0);
+          r1 = cfmac(ue, h1[c], r1);
+        } else {
+          const cx<A> ue = ld2<P>(lk, (int64_t)(a * D + c) * Vh + li);
+          r0 = cfma(ue, h0[c], r0);
+          r1 = cfma(ue, h1[c], r1);
+        }
+      }
+      reconstruct<MU>(sig, r0, r1, acc[a]);
+    }
+  }
+}
+
+// w = B v for one packed Hermitian 2D x 2D block (chunk offset `off`):
+// D chunks of diagonal pairs, then the strictly lower triangle row by row.
+template <int D, int P>
+__device__ __forceinline__ void herm_apply(const void *cl, int64_t Vh, int64_t i, int off,
+                                           const cx<typename PT<P>::A> v[2 * D],
+                                           cx<typename PT<P>::A> w[2 * D]) {
+  typedef typename PT<P>::A A;
+  constexpr int n = 2 * D;
+  constexpr int PC = (P == 0) ? 0 : 1;  // clover storage: FP64 for FP64 fields, else FP32
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const cx<A> dg = ld2<PC>(cl, (int64_t)(off + q) * Vh + i);
+    w[2 * q] = scale(dg.x, v[2 * q]);
+    w[2 * q + 1] = scale(dg.y, v[2 * q + 1]);
+  }
+#pragma unroll
+  for (int r = 1; r < n; ++r) {
+#pragma unroll
+    for (int c = 0; c < r; ++c) {
+      const cx<A> a = ld2<PC>(cl, (int64_t)(off + D + r * (r - 1) / 2 + c) * Vh + i);
+      w[r] = cfma(a, v[c], w[r]);
+      w[c] = cfmac(a, v[r], w[c]);
+    }
+  }
+}
+
+// out = B acc (B = both chiral blocks of A or A^{-1}), in place on acc
+template <int D, int P>
+__device__ __forceinline__ void clover_apply(const void *cl, int64_t Vh, int64_t i,
+                                             cx<typename PT<P>::A> acc[D][4]) {
+  typedef typename PT<P>::A A;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    cx<A> v[2 * D], w[2 * D];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[s * D + c] = acc[c][2 * b + s];
+    herm_apply<D, P>(cl, Vh, i, b * 2 * D * D, v, w);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c][2 * b + s] = w[s * D + c];
+  }
+}
+
+template <int D, bool REAL, int P>
+__global__ void __launch_bounds__(128) hop_kernel(HopK k) {
+  typedef typename PT<P>::A A;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k.Vh) return;
+  const size_t roff = (size_t)blockIdx.y * k.stride;
+  const void *in = reinterpret_cast<const char *>(k.in) + roff;
+  void *out = reinterpret_cast<char *>(k.out) + roff;
+  const int64_t Vh = k.Vh;
+  const int L = k.L, Lh = k.Lh, T = k.T, p = k.p;
+  const Site s = site_of(i, p, L, Lh);
+  const A sg = (A)k.sgn;
+  const int64_t slab = (int64_t)k.nch * Vh;  // chunks per [parity][mu] slot
+  auto slot = [&](int par, int mu) -> const void * {
+    const size_t es = (P == 0) ? 16 : (P == 1 ? 8 : 4);
+    return reinterpret_cast<const char *>(k.links) + (size_t)((par * 4 + mu) * slab) * es;
+  };
+  const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
+
+  cx<A> acc[D][4];
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[c][q] = mk(A(0), A(0));
+
+  const int64_t LLh = (int64_t)L * Lh;
+  // mu = 0 (t)
+  {
+    const int tf = (s.t + 1 == T) ? 0 : s.t + 1, tb = (s.t == 0) ? T - 1 : s.t - 1;
+    const int64_t jf = i + (int64_t)(tf - s.t) * L * LLh, jb = i + (int64_t)(tb - s.t) * L * LLh;
+    hop_dir<D, REAL, P, 0, false>(acc, in, Vh, jf, slot(p, 0), i, -sg, P == 2 ? (A)isc[jf] : A(1));
+    hop_dir<D, REAL, P, 0, true>(acc, in, Vh, jb, slot(1 - p, 0), jb, sg, P == 2 ? (A)isc[jb] : A(1));
+  }
+  // mu = 1 (x)
+  {
+    const int xf = (s.x + 1 == L) ? 0 : s.x + 1, xb = (s.x == 0) ? L - 1 : s.x - 1;
+    const int64_t jf = i - (s.x >> 1) + (xf >> 1), jb = i - (s.x >> 1) + (xb >> 1);
+    hop_dir<D, REAL, P, 1, false>(acc, in, Vh, jf, slot(p, 1), i, -sg, P == 2 ? (A)isc[jf] : A(1));
+    hop_dir<D, REAL, P, 1, true>(acc, in, Vh, jb, slot(1 - p, 1), jb, sg, P == 2 ? (A)isc[jb] : A(1));
+  }
+  // mu = 2 (y)
+  {
+    const int yf = (s.y + 1 == L) ? 0 : s.y + 1, yb = (s.y == 0) ? L - 1 : s.y - 1;
+    const int64_t jf = i + (int64_t)(yf - s.y) * Lh, jb = i + (int64_t)(yb - s.y) * Lh;
+    hop_dir<D, REAL, P, 2, false>(acc, in, Vh, jf, slot(p, 2), i, -sg, P == 2 ? (A)isc[jf] : A(1));
+    hop_dir<D, REAL, P, 2, true>(acc, in, Vh, jb, slot(1 - p, 2), jb, sg, P == 2 ? (A)isc[jb] : A(1));
+  }
+  // mu = 3 (z)
+  {
+    const int zf = (s.z + 1 == L) ? 0 : s.z + 1, zb = (s.z == 0) ? L - 1 : s.z - 1;
+    const int64_t jf = i + (int64_t)(zf - s.z) * LLh, jb = i + (int64_t)(zb - s.z) * LLh;
+    hop_dir<D, REAL, P, 3, false>(acc, in, Vh, jf, slot(p, 3), i, -sg, P == 2 ? (A)isc[jf] : A(1));
+    hop_dir<D, REAL, P, 3, true>(acc, in, Vh, jb, slot(1 - p, 3), jb, sg, P == 2 ? (A)isc[jb] : A(1));
+  }
+
+  // ---- epilogue ----
+  const A coef = (A)k.coef;
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[c][q] = scale(coef, acc[c][q]);
+  if (k.mode == HOP_SCALED) {
+    if (k.clover) clover_apply<D, P>(k.clover, Vh, i, acc);
+  } else {
+    const void *self = reinterpret_cast<const char *>(k.self) + roff;
+    const A ssc = (P == 2) ? (A)f16_scales(self, Vh, D)[i] : A(1);
+    cx<A> sv[D][4];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      ld_colour<P>(self, Vh, i, c, sv[c]);
+      if (P == 2)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sv[c][q] = scale(ssc, sv[c][q]);
+    }
+    if (k.clover) {
+      clover_apply<D, P>(k.clover, Vh, i, sv);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[c][q] = acc[c][q] + sv[c][q];
+    } else {
+      const A dg = (A)k.diag;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[c][q] = axpy_r(dg, sv[c][q], acc[c][q]);
+    }
+  }
+  if (P == 0) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[c]));
+  } else if (P == 1) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) st_colour32(out, Vh, i, c, reinterpret_cast<const cx<float> *>(acc[c]));
+  } else {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m = fmaxf(m, fmaxf(fabsf((float)acc[c][q].x), fabsf((float)acc[c][q].y)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      cx<float> v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = mk((float)acc[c][q].x * inv, (float)acc[c][q].y * inv);
+      st_colour16(out, Vh, i, c, v);
+    }
+    f16_scales_w(out, Vh, D)[i] = m;
+  }
+}
+
+// Launch the site-per-thread kernel for (D, REAL) of precision P.
+template <int P>
+int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st) {
+  HopK k;
+  k.out = a.out;
+  k.in = a.in;
+  k.self = a.self;
+  k.links = a.links;
+  k.clover = a.clover;
+  k.T = lat->T;
+  k.L = lat->L;
+  k.Lh = lat->L / 2;
+  k.p = a.out_parity;
+  k.mode = a.mode;
+  k.nch = lat->nch_link;
+  k.Vh = lat->Vh;
+  k.stride = a.field_stride;
+  k.sgn = a.dagger ? -1.0 : 1.0;
+  k.coef = a.coef;
+  k.diag = a.diag;
+  dim3 block(128);
+  dim3 grid((unsigned)((lat->Vh + 127) / 128), (unsigned)a.nrhs);
+  const int d = lat->d;
+  if (lat->is_real) {
+    switch (d) {
+      case 3: hop_kernel<3, true, P><<<grid, block, 0, st>>>(k); break;
+      case 8: hop_kernel<8, true, P><<<grid, block, 0, st>>>(k); break;
+      default: return HR_ERR_UNSUPPORTED;
+    }
+  } else {
+    switch (d) {
+      case 2: hop_kernel<2, false, P><<<grid, block, 0, st>>>(k); break;
+      case 3: hop_kernel<3, false, P><<<grid, block, 0, st>>>(k); break;
+      case 4: hop_kernel<4, false, P><<<grid, block, 0, st>>>(k); break;
+      case 5: hop_kernel<5, false, P><<<grid, block, 0, st>>>(k); break;
+      case 6: hop_kernel<6, false, P><<<grid, block, 0, st>>>(k); break;
+      default: return HR_ERR_UNSUPPORTED;
+    }
+  }
+  return hr_check_launch("hop_kernel");
+}

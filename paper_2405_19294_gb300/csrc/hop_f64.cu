@@ -1,0 +1,4 @@
+// FP64 instantiations of the site-per-thread hopping kernel (hop.cuh).
+#include "hop.cuh"
+
+int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s) { return hop_dispatch<0>(lat, a, s); }

@@ -1,0 +1,141 @@
+// Internal declarations of libhr: the lattice handle, field layouts, small
+// complex helpers and the kernel launchers shared between translation units.
+//
+// Internal layouts (all per parity, all "structure of arrays" over the V/2
+// sites of that parity, checkerboard index i = ((t*L + z)*L + y)*(L/2) + x/2):
+//
+//   spinor field : nchunk 16-byte chunks per site, chunk k of site i at byte
+//                  (k*Vh + i)*16.  FP64: chunk = one complex (double2),
+//                  k = 4*colour + spin.  FP32: chunk = two complex (float4),
+//                  k = 2*colour + spin/2.  FP16: chunk = four complex (4 x
+//                  half2), k = colour, followed by one float scale per site.
+//   links        : [parity][mu][chunk][Vh] of "2-real" chunks (double2,
+//                  float2, half2).  Complex reps: chunk k = entry k = a*d + c
+//                  of the d x d matrix.  Real reps (adjoint): chunk k holds
+//                  entries 2k, 2k+1 (the last one padded with 0 for odd d*d).
+//                  Slot [p][mu] holds the forward link U_R,mu(x) of the sites
+//                  x of parity p.
+//   clover       : [parity][chunk][Vh] double2/float2; per site two
+//                  Hermitian 2d x 2d blocks, each stored as 2d diagonal reals
+//                  (d chunks) then the strictly lower triangle row by row.
+//
+// A warp therefore reads 32 consecutive 8- or 16-byte chunks per access, and
+// neighbour sites along t, z, y are fixed index offsets (x changes xh by 0/1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/hr.h"
+
+#define HR_MAX_D 35
+
+struct hr_cg_work;
+
+struct hr_lattice {
+  int T, L, N, rep, d, is_real;
+  int64_t V, Vh;
+  cudaStream_t stream;
+  int device;
+  int nch_link;          // 2-real chunks per link
+  void *links[3];        // per hr_prec
+  int have_links;
+  double csw;            // clover coefficient given at represent time
+  void *clover_term;     // FP64 packed blocks of csw (i/4) sigma.F (no mass term)
+  double clover_m0;      // m0 of the cached A and A^{-1} below
+  int clover_cached;
+  void *clover_A[2];     // FP64, FP32 packed A = (4+m0) + term
+  void *clover_Ainv[2];  // FP64, FP32 packed A^{-1}
+  void *tmp;             // Schur intermediate spinor (other parity)
+  size_t tmp_bytes;
+  int *dev_err;          // latched device error word
+  double *red_partials;  // reduction scratch: per-block partial sums
+  unsigned *red_count;   // reduction scratch: arrival counter
+  double *red_out;       // reduction result (device)
+  double *red_out_host;  // pinned host mirror
+  hr_cg_work *cg;        // solver workspace (lazily allocated)
+  double hop_launches;   // statistics
+};
+
+// ---------------------------------------------------------------- errors ----
+#define HR_TRY(expr)                 \
+  do {                               \
+    int hr_rc_ = (expr);             \
+    if (hr_rc_ != HR_OK) return hr_rc_; \
+  } while (0)
+
+#define HR_CUDA(call)                            \
+  do {                                           \
+    cudaError_t hr_e_ = (call);                  \
+    if (hr_e_ != cudaSuccess) {                  \
+      hr_note_cuda_error(hr_e_, #call, __FILE__, __LINE__); \
+      return hr_e_ == cudaErrorMemoryAllocation ? HR_ERR_NOMEM : HR_ERR_CUDA; \
+    }                                            \
+  } while (0)
+
+void hr_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+int hr_check_launch(const char *what);
+
+// ------------------------------------------------------------- geometry ----
+struct HrGeom {
+  int T, L, Lh;
+  int64_t Vh;
+};
+
+static inline HrGeom hr_geom(const hr_lattice *lat) {
+  HrGeom g;
+  g.T = lat->T;
+  g.L = lat->L;
+  g.Lh = lat->L / 2;
+  g.Vh = lat->Vh;
+  return g;
+}
+
+// chunks and bytes of one single-parity, single-rhs spinor field
+static inline int hr_spinor_chunks(int d, int prec) {
+  return prec == HR_F64 ? 4 * d : (prec == HR_F32 ? 2 * d : d);
+}
+static inline size_t hr_spinor_field_bytes(int64_t Vh, int d, int prec) {
+  size_t b = (size_t)hr_spinor_chunks(d, prec) * 16u * (size_t)Vh;
+  if (prec == HR_F16) b += 4u * (size_t)Vh;
+  return (b + 255u) & ~(size_t)255u;
+}
+static inline size_t hr_real_size(int prec) { return prec == HR_F64 ? 8 : (prec == HR_F32 ? 4 : 2); }
+
+// ------------------------------------------------------------ launchers ----
+// Hopping kernel epilogue modes.
+enum HopMode {
+  HOP_SCALED = 0,   // out = Ainv (coef * H)      (clover) | coef * H        (no clover)
+  HOP_SELF = 1      // out = A self + coef * H     (clover) | diag*self + coef*H (no clover)
+};
+
+struct HopArgs {
+  void *out;
+  const void *in;         // field hopped from (parity 1-p)
+  const void *self;       // field of parity p for HOP_SELF
+  const void *links;      // internal links of the precision
+  const void *clover;     // packed A (HOP_SELF) or A^{-1} (HOP_SCALED); null = no clover
+  int out_parity;
+  int dagger;
+  int mode;
+  double coef;            // multiplies H
+  double diag;            // multiplies self when no clover
+  size_t field_stride;    // bytes between rhs fields (in, out, self)
+  int nrhs;
+  double *norm_partials;  // optional fused |out|^2 per block (null = off)
+};
+
+int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s);
+int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+
+// dirac.cu
+int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,
+                 int prec, int nrhs, int dagger, cudaStream_t s);
+int hr_ensure_tmp(hr_lattice *lat, size_t bytes);
+int hr_clover_prepare(hr_lattice *lat, double m0);
+
+

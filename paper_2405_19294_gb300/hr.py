@@ -1,0 +1,190 @@
+"""ctypes binding of libhr (include/hr.h): argument marshalling only.
+
+Every computation runs inside libhr's CUDA kernels; this module turns torch
+tensors into device pointers and the current torch stream into the
+library's stream, and raises ``HrError`` on a non-zero status.  Importing it
+fails loudly if ``libhr.so`` has not been built (``__graft_entry__.build()``
+or ``python -m paper_2405_19294_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhr.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hr.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhr.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+_lib = C.CDLL(LIB_PATH)
+
+FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
+REP = {"fund": FUND, "adj": ADJ, "sym": SYM, "asym": ASYM}
+EVEN, ODD, FULL = 0, 1, 2
+F64, F32, F16 = 0, 1, 2
+PREC = {"f64": F64, "f32": F32, "f16": F16}
+
+
+class hr_info(C.Structure):
+    _fields_ = [("T", C.c_int), ("L", C.c_int), ("N", C.c_int), ("rep", C.c_int), ("d", C.c_int),
+                ("is_real", C.c_int), ("volume", C.c_int64), ("half_volume", C.c_int64),
+                ("flops_hop_site", C.c_double), ("bytes_hop_site", C.c_double * 3)]
+
+
+class hr_cg_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_prec", C.c_int),
+                ("inner_tol", C.c_double), ("nrhs", C.c_int), ("check_every", C.c_int)]
+
+
+class hr_cg_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer_steps", C.c_int), ("true_residual", C.c_double),
+                ("seconds", C.c_double), ("hop_launches", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hr_lattice_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "hr_lattice_destroy": (C.c_int, [_P]),
+    "hr_set_stream": (C.c_int, [_P, _P]),
+    "hr_lattice_info": (C.c_int, [_P, C.POINTER(hr_info)]),
+    "hr_field_bytes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "hr_synchronize": (C.c_int, [_P]),
+    "hr_links_from_algebra": (C.c_int, [_P, _P, _P, C.c_double, C.c_int]),
+    "hr_represent_links": (C.c_int, [_P, _P, C.c_int, C.c_double]),
+    "hr_export_represented_links": (C.c_int, [_P, _P]),
+    "hr_export_clover": (C.c_int, [_P, _P, C.c_double, C.c_int]),
+    "hr_pack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int]),
+    "hr_unpack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int]),
+    "hr_dphi": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
+    "hr_norm2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "hr_cg_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
+                              C.POINTER(hr_cg_stats)]),
+    "hr_status_string": (C.c_char_p, [C.c_int]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/hr.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(hr_\w+)\s*\(", txt, re.M)))
+
+
+class HrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib.hr_status_string(status).decode()} ({status})")
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise HrError(rc, what)
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    return t.data_ptr()
+
+
+class Lattice:
+    """One T x L^3 lattice of SU(N) fermions in representation ``rep`` (owns a libhr handle)."""
+
+    def __init__(self, T: int, L: int, N: int, rep: str):
+        import torch
+        h = _P()
+        _check(_lib.hr_lattice_create(T, L, N, REP[rep], C.byref(h)), "hr_lattice_create")
+        self._h = h
+        self.T, self.L, self.N, self.rep = T, L, N, rep
+        info = hr_info()
+        _check(_lib.hr_lattice_info(h, C.byref(info)), "hr_lattice_info")
+        self.d = info.d
+        self.is_real = bool(info.is_real)
+        self.V = info.volume
+        self.Vh = info.half_volume
+        self.flops_hop_site = info.flops_hop_site
+        self.bytes_hop_site = list(info.bytes_hop_site)
+        self.use_stream(torch.cuda.current_stream())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hr_lattice_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def use_stream(self, stream):
+        _check(_lib.hr_set_stream(self._h, C.c_void_p(stream.cuda_stream)), "hr_set_stream")
+
+    def synchronize(self):
+        _check(_lib.hr_synchronize(self._h), "hr_synchronize")
+
+    # -- fields ----------------------------------------------------------
+    def field_bytes(self, parity: int, prec: int, nrhs: int = 1) -> int:
+        n = C.c_size_t()
+        _check(_lib.hr_field_bytes(self._h, parity, prec, nrhs, C.byref(n)), "hr_field_bytes")
+        return n.value
+
+    def new_field(self, parity: int, prec: int, nrhs: int = 1):
+        import torch
+        return torch.zeros(self.field_bytes(parity, prec, nrhs), dtype=torch.uint8, device="cuda")
+
+    def pack(self, internal, canonical, parity: int, prec: int, nrhs: int = 1):
+        _check(_lib.hr_pack_spinor(self._h, _ptr(internal), _ptr(canonical), parity, prec, nrhs),
+               "hr_pack_spinor")
+
+    def unpack(self, canonical, internal, parity: int, prec: int, nrhs: int = 1):
+        _check(_lib.hr_unpack_spinor(self._h, _ptr(canonical), _ptr(internal), parity, prec, nrhs),
+               "hr_unpack_spinor")
+
+    # -- gauge -----------------------------------------------------------
+    def links_from_algebra(self, U, a, eps: float, reunitarise: bool = True):
+        _check(_lib.hr_links_from_algebra(self._h, _ptr(U), _ptr(a), eps, int(reunitarise)),
+               "hr_links_from_algebra")
+
+    def represent_links(self, U, reunitarise: bool = True, csw: float = 0.0):
+        _check(_lib.hr_represent_links(self._h, _ptr(U), int(reunitarise), csw), "hr_represent_links")
+
+    def export_represented_links(self, out):
+        _check(_lib.hr_export_represented_links(self._h, _ptr(out)), "hr_export_represented_links")
+
+    def export_clover(self, out, m0: float, inverse: bool = False):
+        _check(_lib.hr_export_clover(self._h, _ptr(out), m0, int(inverse)), "hr_export_clover")
+
+    # -- operator and solver ---------------------------------------------
+    def dphi(self, out, inp, parity: int, m0: float, csw: float, prec: int, nrhs: int = 1,
+             dagger: bool = False):
+        _check(_lib.hr_dphi(self._h, _ptr(out), _ptr(inp), parity, m0, csw, prec, nrhs, int(dagger)),
+               "hr_dphi")
+
+    def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
+        out = (C.c_double * nrhs)()
+        _check(_lib.hr_norm2(self._h, _ptr(x), parity, prec, nrhs, out), "hr_norm2")
+        return list(out)
+
+    def cg_solve(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
+                 inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,
+                 raise_on_error: bool = True):
+        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every)
+        st = hr_cg_stats()
+        rc = _lib.hr_cg_solve(self._h, _ptr(x), _ptr(b), parity, m0, csw, C.byref(prm), C.byref(st))
+        if rc != 0 and raise_on_error:
+            raise HrError(rc, "hr_cg_solve")
+        return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
+                "true_residual": st.true_residual, "seconds": st.seconds,
+                "hop_launches": st.hop_launches}
+
+
+def lib_handle():
+    """The loaded ctypes library (for tests of the exported symbols)."""
+    return _lib
