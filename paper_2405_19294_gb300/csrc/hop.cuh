@@ -287,9 +287,7 @@ __global__ void __launch_bounds__(128) hop_kernel(HopK k) {
   }
 }
 
-// Launch the site-per-thread kernel for (D, REAL) of precision P.
-template <int P>
-int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st) {
+static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   HopK k;
   k.out = a.out;
   k.in = a.in;
@@ -307,6 +305,13 @@ int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st) {
   k.sgn = a.dagger ? -1.0 : 1.0;
   k.coef = a.coef;
   k.diag = a.diag;
+  return k;
+}
+
+// Launch the site-per-thread kernel for (D, REAL) of precision P.
+template <int P>
+int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st) {
+  const HopK k = make_hopk(lat, a);
   dim3 block(128);
   dim3 grid((unsigned)((lat->Vh + 127) / 128), (unsigned)a.nrhs);
   const int d = lat->d;

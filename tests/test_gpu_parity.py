@@ -190,3 +190,24 @@ def test_errors_are_reported(hr):
     lat2, _ = gpu_lattice(hr, 4, 4, 3, "fund", 1.0, 0.0)
     with pytest.raises(hr.HrError):
         lat2.dphi(lat2.new_field(0, 1), lat2.new_field(0, 1), 0, -0.4, 1.0, 1)  # csw mismatch
+
+
+LARGE = [(4, "sym"), (6, "asym"), (6, "sym"), (4, "adj"), (5, "adj"), (6, "adj"), (5, "asym")]
+
+
+@pytest.mark.parametrize("N,rep", LARGE)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_dphi_parity_large_representations(hr, N, rep, prec):
+    """d_R = 10 ... 35: the colour-split kernel (several thread blocks, ragged tail)."""
+    T, L, m0, eps = 4, 6, -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, 0.0)
+    op = oracle_operator(T, L, N, rep, eps, m0, 0.0)
+    psi = inputs.gaussian_spinor(1, T, L, lat.d)
+    g = op.geom
+    for parity in (0, 2):
+        for dagger in (0, 1):
+            got = _gpu_apply(lat, psi, parity, m0, 0.0, prec, dagger)[0]
+            ref = _oracle_apply(op, psi[0], parity, dagger)
+            mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+            err = rel_err(got, ref, mask)
+            assert err < TOL[prec], (parity, dagger, err)
