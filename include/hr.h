@@ -64,7 +64,7 @@ typedef enum {
   HR_ERR_STATE = -4,         /* call out of order, e.g. hr_dphi before links */
   HR_ERR_BREAKDOWN = -5,     /* solver breakdown: <p,Ap> <= 0 or non-finite */
   HR_ERR_NOT_CONVERGED = -6, /* solver hit maxit before the tolerance */
-  HR_ERR_UNSUPPORTED = -7,   /* combination not built (e.g. clover with d > 15) */
+  HR_ERR_UNSUPPORTED = -7,   /* combination not built (e.g. clover with d > 8) */
   HR_ERR_DEVICE = -8         /* a kernel-side guard latched an error */
 } hr_status;
 
@@ -139,7 +139,7 @@ int hr_links_from_algebra(hr_lattice *lat, double *U_dev, const double *a_dev, d
  *                then the last row times conj(det))
  *   csw        : clover coefficient; != 0 also builds the clover term
  *                c_sw (i/4) sigma.Fhat from U_R (Sec. 3.1, clover) for
- *                d <= 15, else HR_ERR_UNSUPPORTED
+ *                d <= 8, else HR_ERR_UNSUPPORTED
  * Synchronous with respect to the lattice's stream. */
 int hr_represent_links(hr_lattice *lat, const double *U_dev, int reunitarise, double csw);
 
@@ -183,6 +183,25 @@ int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, d
  * Result written to host memory; synchronises the stream. */
 int hr_norm2(hr_lattice *lat, const void *x, int parity, int prec, int nrhs,
              double *out_host);
+
+/* Variant of hr_norm2 that allocates nothing (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc/cudaFree: code running while a
+ * stream is captured into a CUDA graph, code whose device memory all comes
+ * from a framework's pool allocator, code in host callbacks or under a fixed
+ * memory budget.  Its reduction scratch is a file-scope device array of about
+ * 312 KB (partial sums and arrival counters for up to 16 right-hand sides),
+ * present on every GPU that loads the library until the process exits.
+ *   x           : device, internal field(s) as for hr_norm2 (read)
+ *   half_volume : V/2 of the lattice; d: d_R; parity, prec, nrhs as for hr_norm2
+ *   out_dev     : device, double[nrhs], receives |x_r|^2 (written)
+ *   stream      : cudaStream_t the work is queued on (asynchronous; no sync)
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  Every call shares the one array, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Errors: HR_ERR_ARG for nrhs > 16 or a bad argument, HR_ERR_CUDA. */
+int hr_norm2_static(const void *x, int64_t half_volume, int d, int parity, int prec, int nrhs,
+                    double *out_dev, void *stream);
 
 /* ---- solver (Sec. 3.3) ----------------------------------------------------- */
 

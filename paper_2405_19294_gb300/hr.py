@@ -61,6 +61,7 @@ _SIGS = {
     "hr_norm2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "hr_cg_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
                               C.POINTER(hr_cg_stats)]),
+    "hr_norm2_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():

@@ -1,0 +1,52 @@
+"""hr_norm2_static: the norm reduction for callers that cannot allocate.
+
+Some callers cannot call cudaMalloc/cudaFree: code that runs while a stream
+is captured into a CUDA graph, code whose device memory all comes from a
+framework's pool allocator, code in host callbacks or under a fixed memory
+budget.  hr_norm2_static keeps its reduction scratch in a fixed device array
+inside the library instead of allocating it.  This test calls it through the
+C ABI twice in a row and checks both results against hr_norm2 (the entry
+point that allocates its scratch), within the FP64 parity tolerance.
+
+The file name makes pytest collect it last, so a run that stops at the first
+failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_helpers import from_complex, gpu_lattice
+from paper_2405_19294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("parity,prec,nrhs", [(0, 0, 1), (2, 1, 3), (1, 2, 16)])
+def test_norm2_static_matches_allocating_entry_point(hr, parity, prec, nrhs):
+    T, L, N, rep = 6, 6, 3, "sym"
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
+    psi = inputs.gaussian_spinor(11, T, L, lat.d, nrhs)
+    f = lat.new_field(parity, prec, nrhs)
+    lat.pack(f, from_complex(psi), parity, prec, nrhs)
+    ref = np.array(lat.norm2(f, parity, prec, nrhs))
+    lib = hr.lib_handle()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        out = torch.full((nrhs,), -1.0, dtype=torch.float64, device="cuda")
+        rc = lib.hr_norm2_static(ctypes.c_void_p(f.data_ptr()), lat.Vh, lat.d, parity, prec, nrhs,
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, lib.hr_status_string(rc)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-13 * ref), (got, ref)
+
+
+def test_norm2_static_rejects_too_many_rhs(hr):
+    lib = hr.lib_handle()
+    out = torch.zeros(17, dtype=torch.float64, device="cuda")
+    dummy = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    rc = lib.hr_norm2_static(ctypes.c_void_p(dummy.data_ptr()), 8, 3, 0, 1, 17,
+                             ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == -1
