@@ -322,7 +322,7 @@ def main():
     roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(gbs / world / peaks["hbm_gbs"], 4), "peak_kind": kind,
             "traffic": (round(traffic * sites / 2) if traffic else None),
-            "kernel": "hop_kernel<3,false,1> (2 launches per Dhat)"}
+            "kernel": f"hop_kernel<3,false,1>, tuned shape (G, block) = {lat.tuned_shape(hr.F32)}, 2 launches per Dhat"}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

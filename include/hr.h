@@ -215,6 +215,22 @@ int hr_norm2_static(const void *x, int64_t half_volume, int d, int parity, int p
 int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
                 const hr_cg_params *params, hr_cg_stats *stats);
 
+/* The hopping-kernel launch shape the autotuner chose for this lattice at
+ * (prec, nrhs, clover): split_g * 1000 + threads per block (split_g = 0: one
+ * site per thread; G > 0: G threads per site), or -1 if not tuned yet.  The
+ * first hr_dphi / hr_cg_solve call for a new shape key times the candidate
+ * shapes on the caller's stream (make it outside any stream capture). */
+int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover);
+
+/* The candidate shapes for this lattice at (prec, clover), encoded as above,
+ * into out[0..max); returns how many exist (may exceed max) or an error. */
+int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clover, int *out, int max);
+
+/* Pin the shape for (prec, nrhs, clover) instead of timing candidates
+ * (reproducible runs, tests of every shape).  HR_ERR_ARG unless `shape` is
+ * one of the candidates. */
+int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape);
+
 /* Human-readable text of an hr_status. */
 const char *hr_status_string(int status);
 

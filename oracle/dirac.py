@@ -161,11 +161,10 @@ def clover_leaves(UR: np.ndarray, geom: Geometry, mu: int, nu: int,
     xmm_pn = fw[nu][xmm]
     xmm_mn = bw[nu][xmm]
     xmn_pm = fw[mu][xmn]
-    Um, Un = UR[:, mu], UR[:, nu]
-    q = Um[x] @ Un[xpm] @ _dag(Um[xpn]) @ _dag(Un[x])
-    q = q + Un[x] @ _dag(Um[xmm_pn]) @ _dag(Un[xmm]) @ Um[xmm]
-    q = q + _dag(Um[xmm]) @ _dag(Un[xmm_mn]) @ Um[xmm_mn] @ Un[xmn]
-    q = q + _dag(Un[xmn]) @ Um[xmn] @ Un[xmn_pm] @ _dag(Um[x])
+    q = UR[x, mu] @ UR[xpm, nu] @ _dag(UR[xpn, mu]) @ _dag(UR[x, nu])
+    q = q + UR[x, nu] @ _dag(UR[xmm_pn, mu]) @ _dag(UR[xmm, nu]) @ UR[xmm, mu]
+    q = q + _dag(UR[xmm, mu]) @ _dag(UR[xmm_mn, nu]) @ UR[xmm_mn, mu] @ UR[xmn, nu]
+    q = q + _dag(UR[xmn, nu]) @ UR[xmn, mu] @ UR[xmn_pm, nu] @ _dag(UR[x, mu])
     return q
 
 
@@ -185,6 +184,7 @@ def clover_matrix(UR: np.ndarray, geom: Geometry, m0: float, csw: float,
     if sites is None:
         sites = np.arange(geom.V)
     d = UR.shape[-1]
+    sites = np.asarray(sites)
     A = np.zeros((len(sites), 4 * d, 4 * d), dtype=complex)
     A += (4.0 + m0) * np.eye(4 * d)
     if csw != 0.0:
@@ -198,25 +198,75 @@ def clover_matrix(UR: np.ndarray, geom: Geometry, m0: float, csw: float,
     return A
 
 
+# ------------------------------------------------------------ lazy links ---
+class LazyRepresentedField:
+    """U_R[V][4][d][d] with the time-boundary sign, evaluated only where indexed.
+
+    ``link_fn(sites)`` returns the fundamental links U[len(sites)][4][N][N] of
+    the given sites.  Indexing with ``[sites, mu]`` computes (and caches) U_R
+    exactly as ``represented_field`` does, so a full-size lattice can be
+    checked at sampled sites without materialising the whole field.
+    """
+
+    def __init__(self, link_fn, N: int, rep: str, geom: Geometry):
+        self.link_fn, self.N, self.rep, self.geom = link_fn, N, rep, geom
+        self.d = sun.rep_dim(N, rep)
+        self.shape = (geom.V, 4, self.d, self.d)
+        self._cache = {}
+
+    def _site_links(self, sites):
+        todo = np.unique(np.asarray([x for x in np.unique(sites) if x not in self._cache], dtype=np.int64))
+        if len(todo):
+            UR = sun.represent(self.link_fn(todo), self.N, self.rep)
+            last = self.geom.coords[todo, 0] == self.geom.T - 1
+            UR[last, 0] *= -1.0
+            for k, x in enumerate(todo):
+                self._cache[int(x)] = UR[k]
+        return np.array([self._cache[int(x)] for x in np.asarray(sites).ravel()]).reshape(
+            np.shape(sites) + (4, self.d, self.d))
+
+    def __getitem__(self, key):
+        sites, mu = key
+        return self._site_links(np.asarray(sites))[..., mu, :, :]
+
+
 # --------------------------------------------------------------- D and D^ ---
 class WilsonOperator:
-    """D_R on one gauge background.  ``A`` is None for c_sw = 0 (then A = 4+m0)."""
+    """D_R on one gauge background.  ``A`` is None for c_sw = 0 (then A = 4+m0).
 
-    def __init__(self, U: np.ndarray, N: int, rep: str, geom: Geometry, m0: float,
-                 csw: float = 0.0):
+    With ``link_fn`` instead of ``U`` the represented field is evaluated lazily
+    (``LazyRepresentedField``) and the clover matrix only at the sites asked for.
+    """
+
+    def __init__(self, U, N: int, rep: str, geom: Geometry, m0: float,
+                 csw: float = 0.0, link_fn=None):
         self.N, self.rep, self.geom, self.m0, self.csw = N, rep, geom, m0, csw
         self.d = sun.rep_dim(N, rep)
-        self.UR = represented_field(U, N, rep, geom)
-        self.A = clover_matrix(self.UR, geom, m0, csw) if csw != 0.0 else None
+        self.lazy = link_fn is not None
+        if self.lazy:
+            self.UR = LazyRepresentedField(link_fn, N, rep, geom)
+            self.A = None
+            self._A_cache = {}
+        else:
+            self.UR = represented_field(U, N, rep, geom)
+            self.A = clover_matrix(self.UR, geom, m0, csw) if csw != 0.0 else None
 
     # diagonal part --------------------------------------------------------
     def apply_A(self, psi, sites, dagger=False, inverse=False):
         """A(x) psi(x) (or its adjoint / inverse) at ``sites``; psi is over those sites."""
         d = self.d
-        if self.A is None:
+        if self.A is None and not (self.lazy and self.csw != 0.0):
             c = 4.0 + self.m0
             return psi / c if inverse else psi * c
-        A = self.A[sites]
+        if self.lazy:
+            need = [int(x) for x in sites if int(x) not in self._A_cache]
+            if need:
+                An = clover_matrix(self.UR, self.geom, self.m0, self.csw, np.array(need))
+                for k, x in enumerate(need):
+                    self._A_cache[x] = An[k]
+            A = np.array([self._A_cache[int(x)] for x in sites])
+        else:
+            A = self.A[sites]
         if dagger:
             A = _dag(A)
         v = psi.reshape(len(sites), 4 * d)
@@ -248,18 +298,21 @@ class WilsonOperator:
         g = self.geom
         s = -1 if dagger else 1
         q = 1 - parity
-        psi_p = np.where((g.parity == parity)[:, None, None], psi, 0.0)
         if sites is None:
             sites = g.sites_of_parity(parity)
-        # the opposite-parity sites that the outputs at `sites` depend on
+        sites = np.asarray(sites)
+        assert np.all(g.parity[sites] == parity)
+        # the opposite-parity sites that the outputs at `sites` depend on; the
+        # hops from them read psi only on their (parity-p) neighbours, so psi's
+        # values on parity q never enter
         nb = np.unique(np.concatenate([g.fwd[:, sites].ravel(), g.bwd[:, sites].ravel()]))
         assert np.all(g.parity[nb] == q)
         t = np.zeros_like(psi)
-        t[nb] = -0.5 * hopping(self.UR, psi_p, g, s, nb)          # D_qp psi_p
+        t[nb] = -0.5 * hopping(self.UR, psi, g, s, nb)            # D_qp psi_p
         t[nb] = self.apply_A(t[nb], nb, dagger=dagger, inverse=True)  # A_qq^{-1}
         out = np.zeros_like(psi)
         u = -0.5 * hopping(self.UR, t, g, s, sites)                 # D_pq t
-        out[sites] = self.apply_A(psi_p[sites], sites, dagger=dagger) - u
+        out[sites] = self.apply_A(psi[sites], sites, dagger=dagger) - u
         return out
 
 

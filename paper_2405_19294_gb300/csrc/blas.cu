@@ -16,9 +16,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "blas.cuh"
-#include "cplx.cuh"
-#include "hr_internal.h"
+#include "blas_dev.cuh"
 
 int hr_blas_blocks(int64_t Vh) {
   int64_t nb = (Vh + 255) / 256;
@@ -27,278 +25,54 @@ int hr_blas_blocks(int64_t Vh) {
   return (int)nb;
 }
 
-// block-wide FP64 sum; result valid in thread 0
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = 0.0;
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (l < nw) ? sh[l] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  }
-  return v;
-}
-
-// Publish this block's partial; the last block of this rhs sums all partials in
-// block order and applies `finish`.  Returns nothing; writes red.out[rhs].
-__device__ void reduce_publish(double v, const RedArgs &red, int finish, int nsub) {
-  const int rhs = blockIdx.y / nsub;
-  const int nparts = gridDim.x * nsub;
-  double s = block_sum(v);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    red.partials[(size_t)rhs * 2 * HR_RED_MAXBLK + (blockIdx.y % nsub) * gridDim.x + blockIdx.x] = s;
-    __threadfence();
-    const unsigned prev = atomicAdd(&red.count[rhs], 1u);
-    last = (prev == (unsigned)nparts - 1u);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // fixed-order sum of the partials by one warp
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    for (int b = threadIdx.x; b < nparts; b += 32)
-      t += ((volatile double *)red.partials)[(size_t)rhs * 2 * HR_RED_MAXBLK + b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  }
-  if (threadIdx.x == 0) {
-    red.out[rhs] = t;
-    red.count[rhs] = 0u;
-    if (finish == RED_ALPHA) {
-      // alpha = rr / pAp, frozen (0) once rr reached the stop threshold or on breakdown
-      const double rr = red.rr[rhs];
-      double al = 0.0;
-      if (rr > red.stop[rhs]) {
-        if (t > 0.0 && isfinite(t)) al = rr / t;
-        else atomicExch(red.err, 1);
-      }
-      red.alpha[rhs] = al;
-      if (red.iters && al != 0.0) red.iters[rhs] += 1;
-    } else if (finish == RED_BETA) {
-      const double rr = red.rr[rhs];
-      red.beta[rhs] = (rr > 0.0 && red.alpha[rhs] != 0.0) ? t / rr : 0.0;
-      red.rr_next[rhs] = (red.alpha[rhs] != 0.0) ? t : rr;
-    }
-  }
-}
-
 // ---------------------------------------------------------------- kernels --
+// grid: (blocks, nrhs * nsub); result slot = blockIdx.y / nsub; the parts of a
+// slot are its nsub sub-fields x gridDim.x blocks.
+#define SLOT_ARGS(nsub) (blockIdx.y / (nsub)), ((blockIdx.y % (nsub)) * gridDim.x + blockIdx.x), (gridDim.x * (nsub))
+#define SITE_RANGE ((int64_t)blockIdx.x * blockDim.x + threadIdx.x), ((int64_t)gridDim.x * blockDim.x)
+
 template <int P>
 __global__ void norm2_kernel(const void *x, FieldDesc f, RedArgs red, int finish) {
-  typedef typename PT<P>::A A;
   const char *base = reinterpret_cast<const char *>(x) + (size_t)blockIdx.y * f.fb;
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < f.Vh; i += (int64_t)gridDim.x * blockDim.x) {
-    A s = 0;
-    for (int c = 0; c < f.d; ++c) {
-      cx<A> v[4];
-      ld_colour<P>(base, f.Vh, i, c, v);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s += v[q].x * v[q].x + v[q].y * v[q].y;
-    }
-    double sd = (double)s;
-    if (P == 2) {
-      const double sc = (double)f16_scales(base, f.Vh, f.d)[i];
-      sd *= sc * sc;
-    }
-    acc += sd;
-  }
-  reduce_publish(acc, red, finish, f.nsub);
+  const double acc = norm2_sites<P>(base, f.Vh, f.d, SITE_RANGE);
+  reduce_publish(acc, red, finish, SLOT_ARGS(f.nsub));
 }
 
-// load colour c of site i (FP16 scaled back)
-template <int P>
-__device__ __forceinline__ void ldc(const char *f, int64_t Vh, int d, int64_t i, int c,
-                                    cx<typename PT<P>::A> v[4]) {
-  ld_colour<P>(f, Vh, i, c, v);
-  if (P == 2) {
-    const float s = f16_scales(f, Vh, d)[i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = scale((typename PT<P>::A)s, v[q]);
-  }
-}
-
-// store colour c (FP16: divided by the given site scale, `inv` = 1/scale)
-template <int P>
-__device__ __forceinline__ void stc(char *f, int64_t Vh, int64_t i, int c, const cx<typename PT<P>::A> v[4],
-                                    float inv) {
-  if (P == 0) st_colour64(f, Vh, i, c, reinterpret_cast<const cx<double> *>(v));
-  else if (P == 1) st_colour32(f, Vh, i, c, reinterpret_cast<const cx<float> *>(v));
-  else {
-    cx<float> w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w[q] = mk((float)v[q].x * inv, (float)v[q].y * inv);
-    st_colour16(f, Vh, i, c, w);
-  }
-}
-
-// x += alpha p ; r -= alpha Ap ; rr_new = |r|^2   (x, r: precision PR; p, Ap: PP)
 template <int PR, int PP>
 __global__ void cg_xr_kernel(void *x, void *r, const void *p, const void *Ap, FieldDesc fr, FieldDesc fp,
                              RedArgs red) {
   typedef typename PT<PR>::A AR;
   const int rhs = blockIdx.y / fr.nsub;
-  char *xb = reinterpret_cast<char *>(x) + (size_t)blockIdx.y * fr.fb;
-  char *rb = reinterpret_cast<char *>(r) + (size_t)blockIdx.y * fr.fb;
-  const char *pb = reinterpret_cast<const char *>(p) + (size_t)blockIdx.y * fp.fb;
-  const char *ab = reinterpret_cast<const char *>(Ap) + (size_t)blockIdx.y * fp.fb;
   const AR al = (AR)red.alpha[rhs];
   double acc = 0.0;
-  if (al != (AR)0) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fr.Vh;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      AR s = 0;
-      for (int c = 0; c < fr.d; ++c) {
-        cx<AR> xv[4], rv[4];
-        cx<typename PT<PP>::A> pv[4], av[4];
-        ldc<PR>(xb, fr.Vh, fr.d, i, c, xv);
-        ldc<PR>(rb, fr.Vh, fr.d, i, c, rv);
-        ldc<PP>(pb, fp.Vh, fp.d, i, c, pv);
-        ldc<PP>(ab, fp.Vh, fp.d, i, c, av);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          xv[q] = mk(fma(al, (AR)pv[q].x, xv[q].x), fma(al, (AR)pv[q].y, xv[q].y));
-          rv[q] = mk(fma(-al, (AR)av[q].x, rv[q].x), fma(-al, (AR)av[q].y, rv[q].y));
-          s += rv[q].x * rv[q].x + rv[q].y * rv[q].y;
-        }
-        stc<PR>(xb, fr.Vh, i, c, xv, 1.f);
-        stc<PR>(rb, fr.Vh, i, c, rv, 1.f);
-      }
-      acc += (double)s;
-    }
-  }
-  reduce_publish(acc, red, RED_BETA, fr.nsub);
+  if (al != (AR)0)
+    acc = cg_xr_sites<PR, PP>(reinterpret_cast<char *>(x) + (size_t)blockIdx.y * fr.fb,
+                              reinterpret_cast<char *>(r) + (size_t)blockIdx.y * fr.fb,
+                              reinterpret_cast<const char *>(p) + (size_t)blockIdx.y * fp.fb,
+                              reinterpret_cast<const char *>(Ap) + (size_t)blockIdx.y * fp.fb, fr.Vh, fr.d, al,
+                              SITE_RANGE);
+  reduce_publish(acc, red, RED_BETA, SLOT_ARGS(fr.nsub));
 }
 
-// p = r + beta p   (r: PR, p: PP)
 template <int PR, int PP>
 __global__ void cg_p_kernel(const void *r, void *p, FieldDesc fr, FieldDesc fp, const double *beta,
                             const double *alpha) {
-  typedef typename PT<PP>::A AP;
   const int rhs = blockIdx.y / fr.nsub;
   if (alpha && alpha[rhs] == 0.0) return;  // frozen right-hand side
-  const char *rb = reinterpret_cast<const char *>(r) + (size_t)blockIdx.y * fr.fb;
-  char *pb = reinterpret_cast<char *>(p) + (size_t)blockIdx.y * fp.fb;
-  const AP be = (AP)beta[rhs];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fr.Vh; i += (int64_t)gridDim.x * blockDim.x) {
-    float inv = 1.f;
-    if (PP == 2) {  // first pass: the new site maximum
-      float m = 0.f;
-      for (int c = 0; c < fr.d; ++c) {
-        cx<typename PT<PR>::A> rv[4];
-        cx<AP> pv[4];
-        ldc<PR>(rb, fr.Vh, fr.d, i, c, rv);
-        ldc<PP>(pb, fp.Vh, fp.d, i, c, pv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          m = fmaxf(m, fabsf((float)fma(be, pv[q].x, (AP)rv[q].x)));
-          m = fmaxf(m, fabsf((float)fma(be, pv[q].y, (AP)rv[q].y)));
-        }
-      }
-      inv = m > 0.f ? 1.f / m : 0.f;
-      // second pass below reads the old p again before overwriting it, so the
-      // scale is written last
-      for (int c = 0; c < fr.d; ++c) {
-        cx<typename PT<PR>::A> rv[4];
-        cx<AP> pv[4];
-        ldc<PR>(rb, fr.Vh, fr.d, i, c, rv);
-        ldc<PP>(pb, fp.Vh, fp.d, i, c, pv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) pv[q] = mk(fma(be, pv[q].x, (AP)rv[q].x), fma(be, pv[q].y, (AP)rv[q].y));
-        stc<PP>(pb, fp.Vh, i, c, pv, inv);
-      }
-      f16_scales_w(pb, fp.Vh, fp.d)[i] = m;
-    } else {
-      for (int c = 0; c < fr.d; ++c) {
-        cx<typename PT<PR>::A> rv[4];
-        cx<AP> pv[4];
-        ldc<PR>(rb, fr.Vh, fr.d, i, c, rv);
-        ldc<PP>(pb, fp.Vh, fp.d, i, c, pv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) pv[q] = mk(fma(be, pv[q].x, (AP)rv[q].x), fma(be, pv[q].y, (AP)rv[q].y));
-        stc<PP>(pb, fp.Vh, i, c, pv, inv);
-      }
-    }
-  }
+  cg_p_sites<PR, PP>(reinterpret_cast<const char *>(r) + (size_t)blockIdx.y * fr.fb,
+                     reinterpret_cast<char *>(p) + (size_t)blockIdx.y * fp.fb, fr.Vh, fr.d,
+                     (typename PT<PP>::A)beta[rhs], SITE_RANGE);
 }
 
-// y = a * x + b * y   with per-rhs a, b (host scalars in arrays), precisions PX -> PY;
-// b == 0 overwrites y (y may hold anything).  Optional |y|^2 reduction.
 template <int PX, int PY>
 __global__ void axpby_kernel(const void *x, void *y, FieldDesc fx, FieldDesc fy, const double *a, const double *b,
                              RedArgs red, int want_norm) {
   typedef typename PT<PY>::A AY;
   const int rhs = blockIdx.y / fx.nsub;
-  const char *xb = reinterpret_cast<const char *>(x) + (size_t)blockIdx.y * fx.fb;
-  char *yb = reinterpret_cast<char *>(y) + (size_t)blockIdx.y * fy.fb;
-  const AY av = (AY)a[rhs], bv = (AY)b[rhs];
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fx.Vh; i += (int64_t)gridDim.x * blockDim.x) {
-    float inv = 1.f;
-    if (PY == 2) {
-      float m = 0.f;
-      for (int c = 0; c < fx.d; ++c) {
-        cx<typename PT<PX>::A> xv[4];
-        cx<AY> yv[4];
-        ldc<PX>(xb, fx.Vh, fx.d, i, c, xv);
-        if (bv != (AY)0) ldc<PY>(yb, fy.Vh, fy.d, i, c, yv);
-        else
-#pragma unroll
-          for (int q = 0; q < 4; ++q) yv[q] = mk((AY)0, (AY)0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          m = fmaxf(m, fabsf((float)(av * (AY)xv[q].x + bv * yv[q].x)));
-          m = fmaxf(m, fabsf((float)(av * (AY)xv[q].y + bv * yv[q].y)));
-        }
-      }
-      inv = m > 0.f ? 1.f / m : 0.f;
-      AY s = 0;
-      for (int c = 0; c < fx.d; ++c) {
-        cx<typename PT<PX>::A> xv[4];
-        cx<AY> yv[4];
-        ldc<PX>(xb, fx.Vh, fx.d, i, c, xv);
-        if (bv != (AY)0) ldc<PY>(yb, fy.Vh, fy.d, i, c, yv);
-        else
-#pragma unroll
-          for (int q = 0; q < 4; ++q) yv[q] = mk((AY)0, (AY)0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          yv[q] = mk(av * (AY)xv[q].x + bv * yv[q].x, av * (AY)xv[q].y + bv * yv[q].y);
-          s += yv[q].x * yv[q].x + yv[q].y * yv[q].y;
-        }
-        stc<PY>(yb, fy.Vh, i, c, yv, inv);
-      }
-      f16_scales_w(yb, fy.Vh, fy.d)[i] = m;
-      acc += (double)s;
-    } else {
-      AY s = 0;
-      for (int c = 0; c < fx.d; ++c) {
-        cx<typename PT<PX>::A> xv[4];
-        cx<AY> yv[4];
-        ldc<PX>(xb, fx.Vh, fx.d, i, c, xv);
-        if (bv != (AY)0) ldc<PY>(yb, fy.Vh, fy.d, i, c, yv);
-        else
-#pragma unroll
-          for (int q = 0; q < 4; ++q) yv[q] = mk((AY)0, (AY)0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          yv[q] = mk(fma(av, (AY)xv[q].x, bv * yv[q].x), fma(av, (AY)xv[q].y, bv * yv[q].y));
-          s += yv[q].x * yv[q].x + yv[q].y * yv[q].y;
-        }
-        stc<PY>(yb, fy.Vh, i, c, yv, inv);
-      }
-      acc += (double)s;
-    }
-  }
-  if (want_norm) reduce_publish(acc, red, RED_PLAIN, fx.nsub);
+  const double acc = axpby_sites<PX, PY>(reinterpret_cast<const char *>(x) + (size_t)blockIdx.y * fx.fb,
+                                         reinterpret_cast<char *>(y) + (size_t)blockIdx.y * fy.fb, fx.Vh, fx.d,
+                                         (AY)a[rhs], (AY)b[rhs], SITE_RANGE);
+  if (want_norm) reduce_publish(acc, red, RED_PLAIN, SLOT_ARGS(fx.nsub));
 }
 
 // ---------------------------------------------------------------- launchers

@@ -34,6 +34,7 @@ struct RedArgs {
   const double *stop; // |r|^2 threshold per rhs
   int *err;           // breakdown flag
   int *iters;         // per-rhs count of non-frozen iterations (RED_ALPHA), may be null
+  int *frozen;        // RED_BETA: per-rhs flag rr_next <= stop (multi-lattice hops skip), may be null
 };
 
 int hr_blas_blocks(int64_t Vh);

@@ -72,6 +72,9 @@ static int cg_work(hr_lattice *lat, int prec, size_t bytes) {
 
 static double *S(hr_cg_work *w, int k) { return w->scal + (size_t)k * HR_MAX_RHS; }
 
+int hr_cg_workspace(hr_lattice *lat, int prec, size_t bytes) { return cg_work(lat, prec, bytes); }
+void *hr_cg_field(hr_lattice *lat, int prec, int which) { return lat->cg ? lat->cg->f[prec][which] : nullptr; }
+
 struct CgCtx {
   hr_lattice *lat;
   int parity, nrhs, dagger_unused;
@@ -120,6 +123,10 @@ static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap
   check_every &= ~1;  // even: the rr double buffer returns to S_RR0
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // one uncaptured application first: lets the autotuner time the hop shapes
+  // (it cannot while the stream is being captured); t and Ap are scratch
+  HR_TRY(hr_dphi_impl(c.lat, t, p, c.parity, c.m0, c.csw, pp, c.nrhs, 0, c.s));
+  HR_TRY(hr_dphi_impl(c.lat, Ap, t, c.parity, c.m0, c.csw, pp, c.nrhs, 1, c.s));
   const double hops_before = c.lat->hop_launches;  // capture records launches, replays run them
   HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
   int rc = HR_OK;

@@ -374,15 +374,6 @@ extern "C" int hr_export_clover(hr_lattice *lat, double *A_dev, double m0, int i
 }
 
 // ------------------------------------------------------------------ dphi --
-int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s) {
-  switch (prec) {
-    case HR_F64: return hr_launch_hop_f64(lat, a, s);
-    case HR_F32: return hr_launch_hop_f32(lat, a, s);
-    case HR_F16: return hr_launch_hop_f16(lat, a, s);
-  }
-  return HR_ERR_ARG;
-}
-
 static const void *clover_ptr(const hr_lattice *lat, int prec, bool inverse, int parity) {
   const int q = prec == HR_F64 ? 0 : 1;
   const void *base = inverse ? lat->clover_Ainv[q] : lat->clover_A[q];

@@ -30,11 +30,19 @@ struct HopK {
   const void *self;
   const void *links;
   const void *clover;
-  int T, L, Lh, p, mode, nch;
+  int T, L, Lh, p, mode, nch, nrhs;
   int64_t Vh;
   size_t stride;
   double sgn, coef, diag;
 };
+
+// Blocks are numbered right-hand side fastest: block b handles tile b / nrhs
+// of right-hand side b % nrhs, so the nrhs blocks that read the same links run
+// back to back and all but the first find them in L2.
+__device__ __forceinline__ void block_tile(const HopK &k, int64_t &tile, int &rhs) {
+  rhs = (int)(blockIdx.x % (unsigned)k.nrhs);
+  tile = blockIdx.x / (unsigned)k.nrhs;
+}
 
 template <int MU, typename R>
 __device__ __forceinline__ void project(R sig, const cx<R> psi[4], cx<R> &h0, cx<R> &h1) {
@@ -175,12 +183,11 @@ __device__ __forceinline__ void clover_apply(const void *cl, int64_t Vh, int64_t
   }
 }
 
+// The whole stencil for output site i (< Vh) of right-hand side rhs.
 template <int D, bool REAL, int P>
-__global__ void __launch_bounds__(128) hop_kernel(HopK k) {
+__device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
   typedef typename PT<P>::A A;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k.Vh) return;
-  const size_t roff = (size_t)blockIdx.y * k.stride;
+  const size_t roff = (size_t)rhs * k.stride;
   const void *in = reinterpret_cast<const char *>(k.in) + roff;
   void *out = reinterpret_cast<char *>(k.out) + roff;
   const int64_t Vh = k.Vh;
@@ -287,6 +294,31 @@ __global__ void __launch_bounds__(128) hop_kernel(HopK k) {
   }
 }
 
+template <int D, bool REAL, int P>
+__global__ void __launch_bounds__(256) hop_kernel(HopK k) {
+  int64_t tile;
+  int rhs;
+  block_tile(k, tile, rhs);
+  const int64_t i = tile * blockDim.x + threadIdx.x;
+  if (i < k.Vh) hop_site<D, REAL, P>(k, i, rhs);
+}
+
+// Persistent multi-lattice form: every block walks the work list (lattice,
+// tile) with stride gridDim.x; each lattice brings its own descriptor
+// (geometry, fields, links, epilogue).  A lattice whose `frozen` flag is set
+// (its CG has converged) is skipped.
+template <int D, bool REAL, int P>
+__global__ void __launch_bounds__(256) hop_multi_kernel(const HopK *descs, const int2 *items, int nitems,
+                                                        const int *frozen) {
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int2 it = items[w];
+    if (frozen && frozen[it.x]) continue;
+    const HopK k = descs[it.x];
+    const int64_t i = (int64_t)it.y * blockDim.x + threadIdx.x;
+    if (i < k.Vh) hop_site<D, REAL, P>(k, i, 0);
+  }
+}
+
 static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   HopK k;
   k.out = a.out;
@@ -305,15 +337,17 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   k.sgn = a.dagger ? -1.0 : 1.0;
   k.coef = a.coef;
   k.diag = a.diag;
+  k.nrhs = a.nrhs;
   return k;
 }
 
-// Launch the site-per-thread kernel for (D, REAL) of precision P.
+// Launch the site-per-thread kernel for (D, REAL) of precision P with `bs`
+// threads per block (32 ... 256; the autotuner picks it).
 template <int P>
-int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st) {
+int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int bs) {
   const HopK k = make_hopk(lat, a);
-  dim3 block(128);
-  dim3 grid((unsigned)((lat->Vh + 127) / 128), (unsigned)a.nrhs);
+  dim3 block(bs);
+  dim3 grid((unsigned)(((lat->Vh + bs - 1) / bs) * a.nrhs));
   const int d = lat->d;
   if (lat->is_real) {
     switch (d) {

@@ -1,25 +1,36 @@
 // FP32 instantiations of the hopping kernels: one site per thread for
-// d_R <= 8 (hop.cuh), colour-split groups for the large representations
-// (hop_split.cuh).
+// d_R <= 8 (hop.cuh) and colour-split groups (hop_split.cuh) for d_R >= 6;
+// the autotuner in tune.cu chooses among the shapes listed by hr_hop_shapes.
 #include "hop_split.cuh"
 
-int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s) {
+int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh) {
   const int d = lat->d;
-  if (d <= 8) return hop_dispatch<1>(lat, a, s);
+  if (sh.split_g == 0) return hop_dispatch<1>(lat, a, s, sh.bs);
   if (a.clover) return HR_ERR_UNSUPPORTED;
   const HopK k = make_hopk(lat, a);
+  const int g = sh.split_g;
   if (lat->is_real) {
-    switch (d) {
-      case 15: return launch_split<15, true, 1, 4>(k, a.nrhs, s);
-      case 24: return launch_split<24, true, 1, 8>(k, a.nrhs, s);
-      case 35: return launch_split<35, true, 1, 8>(k, a.nrhs, s);
-    }
+    if (d == 8 && g == 2) return launch_split<8, true, 1, 2>(k, a.nrhs, s);
+    if (d == 8 && g == 4) return launch_split<8, true, 1, 4>(k, a.nrhs, s);
+    if (d == 15 && g == 4) return launch_split<15, true, 1, 4>(k, a.nrhs, s);
+    if (d == 15 && g == 8) return launch_split<15, true, 1, 8>(k, a.nrhs, s);
+    if (d == 24 && g == 8) return launch_split<24, true, 1, 8>(k, a.nrhs, s);
+    if (d == 24 && g == 16) return launch_split<24, true, 1, 16>(k, a.nrhs, s);
+    if (d == 35 && g == 8) return launch_split<35, true, 1, 8>(k, a.nrhs, s);
+    if (d == 35 && g == 16) return launch_split<35, true, 1, 16>(k, a.nrhs, s);
   } else {
-    switch (d) {
-      case 10: return launch_split<10, false, 1, 2>(k, a.nrhs, s);
-      case 15: return launch_split<15, false, 1, 4>(k, a.nrhs, s);
-      case 21: return launch_split<21, false, 1, 4>(k, a.nrhs, s);
-    }
+    if (d == 6 && g == 2) return launch_split<6, false, 1, 2>(k, a.nrhs, s);
+    if (d == 10 && g == 2) return launch_split<10, false, 1, 2>(k, a.nrhs, s);
+    if (d == 10 && g == 4) return launch_split<10, false, 1, 4>(k, a.nrhs, s);
+    if (d == 15 && g == 4) return launch_split<15, false, 1, 4>(k, a.nrhs, s);
+    if (d == 15 && g == 8) return launch_split<15, false, 1, 8>(k, a.nrhs, s);
+    if (d == 21 && g == 4) return launch_split<21, false, 1, 4>(k, a.nrhs, s);
+    if (d == 21 && g == 8) return launch_split<21, false, 1, 8>(k, a.nrhs, s);
   }
   return HR_ERR_UNSUPPORTED;
+}
+
+int hr_launch_hop_multi_f32(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                            const int *frozen, cudaStream_t s) {
+  return hop_multi_launch<1>(d, is_real, sh, descs, items, nitems, frozen, s);
 }

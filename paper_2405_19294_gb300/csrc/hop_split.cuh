@@ -20,18 +20,21 @@
 
 #include "hop.cuh"
 
+// One tile of 128/G output sites of right-hand side rhs; `sh` is the block's
+// double-buffered half-spinor staging area.  Every lane of the block must
+// call it (warp barriers inside).
 template <int D, bool REAL, int P, int G>
-__global__ void __launch_bounds__(128) hop_split_kernel(HopK k) {
+__device__ __forceinline__ void hop_split_tile(const HopK &k, int64_t tile, int rhs,
+                                               cx<typename PT<P>::A> (*sh)[128 / G][2 * D]) {
   typedef typename PT<P>::A A;
   constexpr int R = (D + G - 1) / G;      // rows per thread
   constexpr int SPB = 128 / G;            // sites per block
-  __shared__ cx<A> sh[2][SPB][2 * D];     // half-spinor per site, double buffered
   const int g = threadIdx.x % G;
   const int sl = threadIdx.x / G;
-  const int64_t i = (int64_t)blockIdx.x * SPB + sl;
+  const int64_t i = tile * SPB + sl;
   const bool active = i < k.Vh;
   const int64_t ii = active ? i : 0;      // inactive lanes still join the warp barriers
-  const size_t roff = (size_t)blockIdx.y * k.stride;
+  const size_t roff = (size_t)rhs * k.stride;
   const void *in = reinterpret_cast<const char *>(k.in) + roff;
   void *out = reinterpret_cast<char *>(k.out) + roff;
   const int64_t Vh = k.Vh;
@@ -190,9 +193,92 @@ __global__ void __launch_bounds__(128) hop_split_kernel(HopK k) {
 }
 
 template <int D, bool REAL, int P, int G>
+__global__ void __launch_bounds__(128) hop_split_kernel(HopK k) {
+  __shared__ cx<typename PT<P>::A> sh[2][128 / G][2 * D];  // half-spinor per site, double buffered
+  int64_t tile;
+  int rhs;
+  block_tile(k, tile, rhs);
+  hop_split_tile<D, REAL, P, G>(k, tile, rhs, sh);
+}
+
+// Persistent multi-lattice form (work list of (lattice, tile), see hop_multi_kernel).
+template <int D, bool REAL, int P, int G>
+__global__ void __launch_bounds__(128) hop_split_multi_kernel(const HopK *descs, const int2 *items, int nitems,
+                                                              const int *frozen) {
+  __shared__ cx<typename PT<P>::A> sh[2][128 / G][2 * D];
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int2 it = items[w];
+    if (frozen && frozen[it.x]) continue;
+    const HopK k = descs[it.x];
+    hop_split_tile<D, REAL, P, G>(k, it.y, 0, sh);
+    __syncwarp();  // the next item reuses the staging buffers
+  }
+}
+
+template <int D, bool REAL, int P, int G>
 int launch_split(const HopK &k, int nrhs, cudaStream_t st) {
   constexpr int SPB = 128 / G;
-  dim3 grid((unsigned)((k.Vh + SPB - 1) / SPB), (unsigned)nrhs);
+  dim3 grid((unsigned)(((k.Vh + SPB - 1) / SPB) * nrhs));
   hop_split_kernel<D, REAL, P, G><<<grid, 128, 0, st>>>(k);
   return hr_check_launch("hop_split_kernel");
+}
+
+// Kernel entry of the persistent multi-lattice hop for (D, REAL, shape), and
+// its block size; null when the shape does not exist for that d_R.
+template <int P>
+static const void *multi_kernel_ptr(int d, int is_real, HopShape sh, int *block) {
+  *block = sh.split_g ? 128 : sh.bs;
+  if (sh.split_g == 0) {
+    if (is_real) {
+      if (d == 3) return (const void *)hop_multi_kernel<3, true, P>;
+      if (d == 8) return (const void *)hop_multi_kernel<8, true, P>;
+    } else {
+      if (d == 2) return (const void *)hop_multi_kernel<2, false, P>;
+      if (d == 3) return (const void *)hop_multi_kernel<3, false, P>;
+      if (d == 4) return (const void *)hop_multi_kernel<4, false, P>;
+      if (d == 5) return (const void *)hop_multi_kernel<5, false, P>;
+      if (d == 6) return (const void *)hop_multi_kernel<6, false, P>;
+    }
+    return nullptr;
+  }
+  const int g = sh.split_g;
+  if (is_real) {
+    if (d == 8 && g == 2) return (const void *)hop_split_multi_kernel<8, true, P, 2>;
+    if (d == 8 && g == 4) return (const void *)hop_split_multi_kernel<8, true, P, 4>;
+    if (d == 15 && g == 4) return (const void *)hop_split_multi_kernel<15, true, P, 4>;
+    if (d == 15 && g == 8) return (const void *)hop_split_multi_kernel<15, true, P, 8>;
+    if (d == 24 && g == 8) return (const void *)hop_split_multi_kernel<24, true, P, 8>;
+    if (d == 24 && g == 16) return (const void *)hop_split_multi_kernel<24, true, P, 16>;
+    if (d == 35 && g == 8) return (const void *)hop_split_multi_kernel<35, true, P, 8>;
+    if (d == 35 && g == 16) return (const void *)hop_split_multi_kernel<35, true, P, 16>;
+  } else {
+    if (d == 6 && g == 2) return (const void *)hop_split_multi_kernel<6, false, P, 2>;
+    if (d == 10 && g == 2) return (const void *)hop_split_multi_kernel<10, false, P, 2>;
+    if (d == 10 && g == 4) return (const void *)hop_split_multi_kernel<10, false, P, 4>;
+    if (d == 15 && g == 4) return (const void *)hop_split_multi_kernel<15, false, P, 4>;
+    if (d == 15 && g == 8) return (const void *)hop_split_multi_kernel<15, false, P, 8>;
+    if (d == 21 && g == 4) return (const void *)hop_split_multi_kernel<21, false, P, 4>;
+    if (d == 21 && g == 8) return (const void *)hop_split_multi_kernel<21, false, P, 8>;
+  }
+  return nullptr;
+}
+
+// Persistent launch: grid = min(work items, SMs x resident blocks per SM).
+template <int P>
+int hop_multi_launch(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                     const int *frozen, cudaStream_t s) {
+  int block = 0;
+  const void *fn = multi_kernel_ptr<P>(d, is_real, sh, &block);
+  if (!fn) return HR_ERR_UNSUPPORTED;
+  if (nitems <= 0) return HR_OK;
+  int dev = 0, sms = 0, per_sm = 0;
+  HR_CUDA(cudaGetDevice(&dev));
+  HR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > nitems) grid = nitems;
+  void *args[] = {(void *)&descs, (void *)&items, (void *)&nitems, (void *)&frozen};
+  HR_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s));
+  return HR_OK;
 }

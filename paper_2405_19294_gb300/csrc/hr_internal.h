@@ -127,10 +127,34 @@ struct HopArgs {
   double *norm_partials;  // optional fused |out|^2 per block (null = off)
 };
 
+// One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
+// thread kernel with `bs` threads per block; split_g = G > 0 is the
+// colour-split kernel with G threads per site (128 threads per block).
+struct HopShape {
+  int split_g;
+  int bs;
+};
+#define HR_MAX_SHAPES 8
+
+// Candidate shapes for (d, real, precision); clover restricts to split_g = 0.
+int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out);
 int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s);
-int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
-int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
-int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+
+// multi-lattice persistent hop (descs: one HopK per lattice; items: (lattice, tile))
+struct HopK;
+int hr_launch_hop_multi_f64(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                            const int *frozen, cudaStream_t s);
+int hr_launch_hop_multi_f32(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                            const int *frozen, cudaStream_t s);
+int hr_launch_hop_multi_f16(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                            const int *frozen, cudaStream_t s);
+
+// cg.cu: per-lattice solver workspace (5 fields per precision: r, p, Ap, t, x)
+int hr_cg_workspace(hr_lattice *lat, int prec, size_t bytes);
+void *hr_cg_field(hr_lattice *lat, int prec, int which);
 
 // dirac.cu
 int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,

@@ -1,0 +1,153 @@
+// Autotuner for the hopping-kernel launch shape.
+//
+// The best shape depends on d_R, real/complex links, precision and lattice
+// size: the one-site-per-thread kernel with 32..256 threads per block
+// (register-limited occupancy changes with the block size) or the
+// colour-split kernel with G threads per site.  The first launch with a new
+// key (precision, d_R, real, clover, multi-rhs, log2 of the volume) times every
+// candidate shape with CUDA events on the caller's stream (one warm-up and
+// three timed launches each, on the caller's own buffers -- the kernel is a
+// pure function of its inputs, so repeating it is harmless) and keeps the
+// fastest.  While the stream is being captured into a CUDA graph no timing is
+// possible; the cached choice, else the first candidate, is used.  Setting
+// HR_TUNE=0 in the environment disables tuning (first candidate always).
+#include <map>
+#include <mutex>
+#include <stdlib.h>
+#include <string.h>
+
+#include "hr_internal.h"
+
+int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out) {
+  (void)prec;
+  int n = 0;
+  const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
+  if (site) {
+    const int bss[4] = {64, 128, 32, 256};
+    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k]};
+  }
+  if (!clover) {
+    int gs[2] = {0, 0};
+    if (is_real) {
+      if (d == 8) { gs[0] = 2; gs[1] = 4; }
+      if (d == 15) { gs[0] = 4; gs[1] = 8; }
+      if (d == 24 || d == 35) { gs[0] = 8; gs[1] = 16; }
+    } else {
+      if (d == 6) gs[0] = 2;
+      if (d == 10) { gs[0] = 2; gs[1] = 4; }
+      if (d == 15 || d == 21) { gs[0] = 4; gs[1] = 8; }
+    }
+    for (int k = 0; k < 2; ++k)
+      if (gs[k]) out[n++] = HopShape{gs[k], 128};
+  }
+  return n;
+}
+
+static int launch_shape(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s, HopShape sh) {
+  switch (prec) {
+    case HR_F64: return hr_launch_hop_f64(lat, a, s, sh);
+    case HR_F32: return hr_launch_hop_f32(lat, a, s, sh);
+    case HR_F16: return hr_launch_hop_f16(lat, a, s, sh);
+  }
+  return HR_ERR_ARG;
+}
+
+static std::mutex g_mu;
+static std::map<long long, HopShape> g_best;
+
+static long long tune_key(const hr_lattice *lat, int prec, const HopArgs &a) {
+  int lg = 0;
+  while (((int64_t)1 << lg) < lat->Vh) ++lg;
+  int dev = lat->device;
+  return ((((((long long)dev * 4 + prec) * 64 + lat->d) * 2 + lat->is_real) * 2 + (a.clover != nullptr)) * 2 +
+          (a.nrhs > 1)) * 64 + lg;
+}
+
+static bool tuning_enabled() {
+  const char *e = getenv("HR_TUNE");
+  return !(e && e[0] == '0');
+}
+
+int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s) {
+  HopShape shapes[HR_MAX_SHAPES];
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, a.clover != nullptr, shapes);
+  if (n == 0) return HR_ERR_UNSUPPORTED;
+  const long long key = tune_key(lat, prec, a);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_best.find(key);
+    if (it != g_best.end()) return launch_shape(lat, prec, a, s, it->second);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone || n == 1 ||
+      !tuning_enabled())
+    return launch_shape(lat, prec, a, s, shapes[0]);
+  cudaEvent_t e0, e1;
+  HR_CUDA(cudaEventCreate(&e0));
+  HR_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  HopShape best = shapes[0];
+  for (int c = 0; c < n; ++c) {
+    int rc = launch_shape(lat, prec, a, s, shapes[c]);  // warm-up
+    if (rc != HR_OK) continue;
+    HR_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) HR_TRY(launch_shape(lat, prec, a, s, shapes[c]));
+    HR_CUDA(cudaEventRecord(e1, s));
+    HR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = shapes[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_best[key] = best;
+  }
+  return launch_shape(lat, prec, a, s, best);
+}
+
+// Report the tuned shape for the lattice's hop at (prec, nrhs, clover): returns
+// split_g * 1000 + block size, or -1 if that key has not been tuned yet.
+extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover) {
+  if (!lat) return -1;
+  HopArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nrhs = nrhs;
+  a.clover = clover ? (const void *)1 : nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_best.find(tune_key(lat, prec, a));
+  if (it == g_best.end()) return -1;
+  return it->second.split_g * 1000 + it->second.bs;
+}
+
+// Candidate shapes of this lattice's hop, encoded split_g * 1000 + block size.
+extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clover, int *out, int max) {
+  if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16) return HR_ERR_ARG;
+  HopShape shapes[HR_MAX_SHAPES];
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
+  for (int k = 0; k < n && k < max; ++k) out[k] = shapes[k].split_g * 1000 + shapes[k].bs;
+  return n;
+}
+
+// Pin the shape used for (prec, nrhs, clover) on this lattice's size class,
+// bypassing the timing; the shape must be one of the candidates.
+extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape) {
+  if (!lat || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
+  HopShape shapes[HR_MAX_SHAPES];
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
+  for (int k = 0; k < n; ++k)
+    if (shapes[k].split_g * 1000 + shapes[k].bs == shape) {
+      HopArgs a;
+      memset(&a, 0, sizeof(a));
+      a.nrhs = nrhs;
+      a.clover = clover ? (const void *)1 : nullptr;
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_best[tune_key(lat, prec, a)] = shapes[k];
+      return HR_OK;
+    }
+  return HR_ERR_ARG;
+}

@@ -13,7 +13,7 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhr.so")
+LIB_PATH = os.environ.get("HR_LIBRARY") or os.path.join(HERE, "libhr.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hr.h")
 
 if not os.path.exists(LIB_PATH):
@@ -62,6 +62,9 @@ _SIGS = {
     "hr_cg_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
                               C.POINTER(hr_cg_stats)]),
     "hr_norm2_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "hr_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "hr_hop_shape_candidates": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "hr_set_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -167,6 +170,22 @@ class Lattice:
              dagger: bool = False):
         _check(_lib.hr_dphi(self._h, _ptr(out), _ptr(inp), parity, m0, csw, prec, nrhs, int(dagger)),
                "hr_dphi")
+
+    def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
+        """(threads per site group G or 0, threads per block) chosen by the autotuner, or None."""
+        v = _lib.hr_tuned_shape(self._h, prec, nrhs, int(clover))
+        return None if v < 0 else (v // 1000, v % 1000)
+
+    def shape_candidates(self, prec: int, clover: bool = False):
+        buf = (C.c_int * 16)()
+        n = _lib.hr_hop_shape_candidates(self._h, prec, int(clover), buf, 16)
+        if n < 0:
+            raise HrError(n, "hr_hop_shape_candidates")
+        return [(v // 1000, v % 1000) for v in buf[:n]]
+
+    def set_shape(self, prec: int, shape, nrhs: int = 1, clover: bool = False):
+        _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), shape[0] * 1000 + shape[1]),
+               "hr_set_tuned_shape")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
         out = (C.c_double * nrhs)()

@@ -13,7 +13,8 @@ read):
 * gauge input: ``a[site][mu][k]`` with ``k = 0..N*N-2``, i.i.d. N(0,1), drawn
   from one PCG64 stream in exactly that order;
 * spinors: ``psi[rhs][site][spin][colour]`` complex, real and imaginary
-  parts i.i.d. N(0,1) (real part drawn first for each component).
+  parts i.i.d. N(0,1) (real part drawn first for each component); right-hand
+  side r comes from its own stream PCG64([seed, r]).
 """
 from __future__ import annotations
 
@@ -34,12 +35,17 @@ def algebra_coefficients(seed: int, T: int, L: int, N: int) -> np.ndarray:
     return rng.standard_normal((V, 4, N * N - 1))
 
 
-def gaussian_spinor(seed: int, T: int, L: int, d: int, nrhs: int = 1) -> np.ndarray:
-    """Complex Gaussian spinor field psi[nrhs][V][4][d] (complex128)."""
+def gaussian_spinor_rhs(seed: int, T: int, L: int, d: int, r: int) -> np.ndarray:
+    """Right-hand side r of ``gaussian_spinor``: psi[V][4][d] (complex128)."""
     V = T * L * L * L
-    rng = np.random.Generator(np.random.PCG64(seed))
-    re_im = rng.standard_normal((nrhs, V, 4, d, 2))
+    rng = np.random.Generator(np.random.PCG64([seed, r]))
+    re_im = rng.standard_normal((V, 4, d, 2))
     return re_im[..., 0] + 1j * re_im[..., 1]
+
+
+def gaussian_spinor(seed: int, T: int, L: int, d: int, nrhs: int = 1) -> np.ndarray:
+    """Complex Gaussian spinor fields psi[nrhs][V][4][d] (complex128)."""
+    return np.stack([gaussian_spinor_rhs(seed, T, L, d, r) for r in range(nrhs)])
 
 
 def gauge_transform_coefficients(seed: int, T: int, L: int, N: int) -> np.ndarray:

@@ -1,0 +1,121 @@
+"""Full-size workloads, checked on the GPU against the oracle at sampled sites.
+
+The oracle evaluates the represented links and the clover term lazily, only
+in the neighbourhoods of the sampled sites, so the full lattices
+(32^3 x 64 and 24^3 x 48) stay affordable.  Sampled sites always include the
+lattice corners and the time boundary (where the antiperiodic sign sits).
+
+* config 1  SU(3) fund, 32^3 x 64, eps 1.0, m0 -0.4: Dhat in FP64 and FP32;
+            CG plain FP64, mixed FP32, mixed FP16 to 1e-10
+* config 2  SU(2) adj and SU(4) asym, 24^3 x 48, m0 -0.3: Dhat in FP32 and FP16;
+            mixed FP16 / FP32 CG to 1e-10
+* config 3  SU(3) sym with clover csw 1.0, 32^3 x 64, m0 -0.35, 12 rhs: Dhat on all
+            right-hand sides at once in FP32; mixed FP32 CG on all 12 to 1e-10
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, from_complex, to_complex
+from oracle import sun
+from oracle.dirac import Geometry, WilsonOperator
+from paper_2405_19294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CONFIGS = {
+    "c1": dict(N=3, rep="fund", T=64, L=32, eps=1.0, m0=-0.4, csw=0.0, nrhs=1, precs=(0, 1), inner=(0, 1, 2)),
+    "c2_adj": dict(N=2, rep="adj", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
+    "c2_asym": dict(N=4, rep="asym", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
+    "c3": dict(N=3, rep="sym", T=64, L=32, eps=1.0, m0=-0.35, csw=1.0, nrhs=12, precs=(1,), inner=(1,)),
+}
+
+_cache = {}
+
+
+def _setup(hr, name):
+    if name in _cache:
+        return _cache[name]
+    c = CONFIGS[name]
+    T, L, N, rep = c["T"], c["L"], c["N"], c["rep"]
+    lat = hr.Lattice(T, L, N, rep)
+    a = inputs.algebra_coefficients(0, T, L, N)
+    a_d = torch.from_numpy(a).cuda()
+    U = torch.empty((lat.V, 4, N, N, 2), dtype=torch.float64, device="cuda")
+    lat.links_from_algebra(U, a_d, c["eps"], True)
+    lat.represent_links(U, True, c["csw"])
+    del a_d, U
+    g = Geometry(T, L)
+    op = WilsonOperator(None, N, rep, g, c["m0"], c["csw"],
+                        link_fn=lambda s: sun.reunitarise(sun.links_from_algebra(a[s], c["eps"], N)))
+    # samples: corners / time boundary plus random even sites
+    rng = np.random.default_rng(123)
+    even = g.sites_of_parity(0)
+    picks = [g.lex(np.array([t, x, y, z])) for (t, x, y, z) in
+             [(0, 0, 0, 0), (T - 1, L - 1, 0, 0), (T - 1, 0, L - 1, 0), (0, L - 2, L - 1, L - 1),
+              (T - 2, 1, 1, 0), (T // 2, L - 1, L - 1, 0)]]
+    picks = [int(p) for p in picks if g.parity[p] == 0]
+    sites = np.unique(np.concatenate([np.array(picks, dtype=np.int64), rng.choice(even, 10, replace=False)]))
+    _cache[name] = (lat, op, g, sites)
+    return _cache[name]
+
+
+def _load_sources(lat, c, parity, prec):
+    """Pack the Gaussian sources rhs by rhs (host memory: one rhs at a time)."""
+    nrhs = c["nrhs"]
+    f = lat.new_field(parity, prec, nrhs)
+    fb = lat.field_bytes(parity, prec, 1)
+    for r in range(nrhs):
+        psi = inputs.gaussian_spinor_rhs(1, c["T"], c["L"], lat.d, r)
+        lat.pack(f[r * fb:(r + 1) * fb], from_complex(psi), parity, prec, 1)
+    return f
+
+
+def _unpack_rhs(lat, f, parity, prec, r):
+    fb = lat.field_bytes(parity, prec, 1)
+    out = torch.zeros((1, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, f[r * fb:(r + 1) * fb], parity, prec, 1)
+    return to_complex(out)[0]
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_full_size_dhat_sampled(hr, name):
+    c = CONFIGS[name]
+    lat, op, g, sites = _setup(hr, name)
+    check_rhs = [0] if c["nrhs"] == 1 else [0, c["nrhs"] - 1]
+    for prec in c["precs"]:
+        fin = _load_sources(lat, c, 0, prec)
+        fout = lat.new_field(0, prec, c["nrhs"])
+        lat.dphi(fout, fin, 0, c["m0"], c["csw"], prec, c["nrhs"])
+        lat.synchronize()
+        for r in check_rhs:
+            psi = inputs.gaussian_spinor_rhs(1, c["T"], c["L"], lat.d, r)
+            got = _unpack_rhs(lat, fout, 0, prec, r)
+            ref = op.apply_schur(psi, 0, sites=sites)
+            err = np.linalg.norm(got[sites] - ref[sites]) / np.linalg.norm(ref[sites])
+            assert err < TOL[prec], (name, prec, r, err)
+        del fin, fout
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_full_size_cg_to_1e10(hr, name):
+    c = CONFIGS[name]
+    lat, op, g, sites = _setup(hr, name)
+    nrhs = c["nrhs"]
+    fb_ = _load_sources(lat, c, 0, 0)
+    for inner in c["inner"]:
+        fx = lat.new_field(0, 0, nrhs)
+        st = lat.cg_solve(fx, fb_, 0, c["m0"], c["csw"], 1e-10, inner_prec=inner, nrhs=nrhs, check_every=10)
+        assert st["true_residual"] <= 1e-10, (name, inner, st)
+        # oracle residual at the sampled sites of rhs 0: b - Dhat^+ Dhat x
+        x = _unpack_rhs(lat, fx, 0, 0, 0)
+        b = inputs.gaussian_spinor_rhs(1, c["T"], c["L"], lat.d, 0)
+        s2 = np.unique(np.concatenate([sites] + [g.fwd[m][g.fwd[n][sites]] for m in range(4) for n in range(4)]
+                                      + [g.bwd[m][g.bwd[n][sites]] for m in range(4) for n in range(4)]
+                                      + [g.fwd[m][g.bwd[n][sites]] for m in range(4) for n in range(4)]))
+        s2 = s2[g.parity[s2] == 0]
+        y = op.apply_schur(x, 0, sites=s2)
+        Mx = op.apply_schur(y, 0, dagger=True, sites=sites)
+        res = np.linalg.norm(b[sites] - Mx[sites]) / np.linalg.norm(b[sites])
+        assert res < 1e-9, (name, inner, res)
+        del fx

@@ -211,3 +211,31 @@ def test_dphi_parity_large_representations(hr, N, rep, prec):
             mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
             err = rel_err(got, ref, mask)
             assert err < TOL[prec], (parity, dagger, err)
+
+
+@pytest.mark.parametrize("N,rep", [(3, "fund"), (3, "adj"), (3, "sym"), (4, "sym"), (6, "asym"), (5, "adj"),
+                                   (6, "sym"), (6, "adj")])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_every_tuner_shape_is_correct(hr, N, rep, prec):
+    """Each candidate launch shape of the autotuner, pinned in turn, matches the oracle."""
+    T, L, m0, eps = 4, 6, -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, 0.0)
+    op = oracle_operator(T, L, N, rep, eps, m0, 0.0)
+    psi = inputs.gaussian_spinor(7, T, L, lat.d)
+    ref = _oracle_apply(op, psi[0], 0, 0)
+    mask = op.geom.parity == 0
+    shapes = lat.shape_candidates(prec)
+    assert len(shapes) >= 1
+    for sh in shapes:
+        lat.set_shape(prec, sh)
+        got = _gpu_apply(lat, psi, 0, m0, 0.0, prec, 0)[0]
+        assert rel_err(got, ref, mask) < TOL[prec], sh
+        assert lat.tuned_shape(prec) == sh
+
+
+def test_autotuner_records_a_choice(hr):
+    lat, _ = gpu_lattice(hr, 8, 8, 3, "fund", 1.0, 0.0)
+    psi = inputs.gaussian_spinor(8, 8, 8, 3)
+    _gpu_apply(lat, psi, 0, -0.4, 0.0, 1, 0)
+    sh = lat.tuned_shape(1)
+    assert sh is not None and sh in lat.shape_candidates(1)

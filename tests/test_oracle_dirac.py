@@ -291,3 +291,20 @@ def test_fp16_code():
     # |v - decode| <= |v| 2^-24 (to FP32) + scale 2^-11 (to FP16, half ulp at 1) + tiny
     err = np.abs(dec - v)
     assert np.all(err <= np.abs(v) * 2.0 ** -23 + s[:, None].astype(np.float64) * 2.0 ** -11)
+
+
+def test_lazy_evaluation_matches_eager():
+    """The lazily evaluated operator (used for full-size sampled checks) equals the eager one."""
+    N, rep, T, L = 3, "sym", 4, 4
+    g = Geometry(T, L)
+    a = inputs.algebra_coefficients(21, T, L, N)
+    U = sun.reunitarise(sun.links_from_algebra(a, 1.0, N))
+    eager = WilsonOperator(U, N, rep, g, -0.35, 1.0)
+    lazy = WilsonOperator(None, N, rep, g, -0.35, 1.0,
+                          link_fn=lambda s: sun.reunitarise(sun.links_from_algebra(a[s], 1.0, N)))
+    psi = _spinor(T, L, eager.d, 22)
+    sites = g.sites_of_parity(1)[[0, 3, 50, 127]]
+    for dag in (False, True):
+        ref = eager.apply_schur(psi, 1, dagger=dag)
+        got = lazy.apply_schur(psi, 1, dagger=dag, sites=sites)
+        assert np.max(np.abs(got[sites] - ref[sites])) < 1e-13
