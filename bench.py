@@ -161,6 +161,24 @@ def cpu_baseline_leg():
                                         f"{dt * 1e3:.1f} ms each"}
 
 
+# ------------------------------------------------------- multi-process --
+def job_timing(ms_step, world, dist, device=None):
+    """Whole-job step time: the maximum over ranks (replicas run independent
+    lattices, so the job finishes when the slowest rank does).  A host-side
+    reduction of one scalar; no data of the operator crosses ranks."""
+    if dist is None or world == 1:
+        return float(ms_step)
+    import torch
+    t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_step_per_rank, world, ms_job):
+    """Aggregate GB/s over all ranks: every rank moves its own replica's bytes."""
+    return world * bytes_per_step_per_rank / (ms_job * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ main --
 def hop_source_digest():
     h = hashlib.sha256()
@@ -182,6 +200,140 @@ def ncu_traffic(key):
     return rec.get(key)
 
 
+# ------------------------------------------------------------ suite mode --
+def _lattice(hr, inputs, torch, T, L, N, rep, eps, csw, seed=0):
+    lat = hr.Lattice(T, L, N, rep)
+    a = torch.from_numpy(inputs.algebra_coefficients(seed, T, L, N)).cuda()
+    U = torch.empty((lat.V, 4, N, N, 2), dtype=torch.float64, device="cuda")
+    lat.links_from_algebra(U, a, eps, True)
+    lat.represent_links(U, True, csw)
+    del a, U
+    return lat
+
+
+def _pack_rhs(lat, inputs, torch, seed, T, L, nrhs, prec, parity=0):
+    f = lat.new_field(parity, prec, nrhs)
+    fb = lat.field_bytes(parity, prec, 1)
+    for r in range(nrhs):
+        psi = inputs.gaussian_spinor_rhs(seed, T, L, lat.d, r)
+        lat.pack(f[r * fb:(r + 1) * fb], torch.from_numpy(np.stack([psi.real, psi.imag], -1)).cuda(), parity, prec)
+    return f
+
+
+def _timed_cg(lat, fx, fb, m0, csw, inner, nrhs=1, inner_tol=0.0, reps=2):
+    import torch
+    res = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = lat.cg_solve(fx, fb, 0, m0, csw, 1e-10, inner_prec=inner, inner_tol=inner_tol, nrhs=nrhs,
+                           check_every=20, raise_on_error=False)
+        res["wall_s"] = round(time.perf_counter() - t0, 4)
+    return res
+
+
+def run_suite(args):
+    """Measurements of the other workloads (one JSON line each; not the bench line)."""
+    import torch
+    from paper_2405_19294_gb300 import hr, inputs
+    out = []
+    # SU(2) adjoint and SU(4) antisymmetric on 24^3 x 48: mixed-precision CG
+    for N, rep in ((2, "adj"), (4, "asym")):
+        T, L, m0 = 48, 24, -0.3
+        lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+        fb = _pack_rhs(lat, inputs, torch, 1, T, L, 1, hr.F64)
+        fx = lat.new_field(0, hr.F64)
+        line = {"suite": "SU(%d) %s 24^3x48 CG to 1e-10" % (N, rep), "m0": m0}
+        for name, inner, itol in (("fp64", hr.F64, 0.0), ("mixed_fp32", hr.F32, 0.0),
+                                  ("mixed_fp16", hr.F16, 0.0), ("mixed_fp16_itol3e-3", hr.F16, 3e-3)):
+            r = _timed_cg(lat, fx, fb, m0, 0.0, inner, inner_tol=itol)
+            line[name] = {k: r[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
+        for k in list(line):
+            if k.startswith("mixed") and line["fp64"]["wall_s"] > 0:
+                line[k]["speedup_vs_fp64"] = round(line["fp64"]["wall_s"] / line[k]["wall_s"], 2)
+        # Dhat GB/s per precision (L2 flushed between steps)
+        flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+        gb = {}
+        for prec in (hr.F32, hr.F16):
+            fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
+            fo = lat.new_field(0, prec)
+            for _ in range(3):
+                lat.dphi(fo, fi, 0, m0, 0.0, prec)
+            ts = []
+            st = torch.cuda.current_stream()
+            for _ in range(20):
+                flush.sum()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                lat.dphi(fo, fi, 0, m0, 0.0, prec)
+                e1.record(st)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = float(np.median([a_.elapsed_time(b_) for a_, b_ in ts]))
+            w = 4 if prec == hr.F32 else 2
+            gb[("fp32", "fp32", "fp16")[prec]] = round(bytes_per_even_site(N, rep, w) * lat.Vh / ms / 1e6, 1)
+        line["dhat_gbs"] = gb
+        out.append(line)
+        print(json.dumps(line), flush=True)
+        lat.close()
+        del fb, fx
+        torch.cuda.empty_cache()
+    # SU(3) sextet with clover, 32^3 x 64, 12 right-hand sides
+    T, L, N, rep, m0, csw, nr = 64, 32, 3, "sym", -0.35, 1.0, 12
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, csw)
+    fb = _pack_rhs(lat, inputs, torch, 1, T, L, nr, hr.F64)
+    fx = lat.new_field(0, hr.F64, nr)
+    line = {"suite": "SU(3) sym csw=1 32^3x64 12 rhs CG to 1e-10", "m0": m0}
+    r = _timed_cg(lat, fx, fb, m0, csw, hr.F32, nrhs=nr, reps=1)
+    line["mixed_fp32_12rhs"] = {k: r[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
+    line["mixed_fp32_12rhs"]["seconds_per_rhs"] = round(r["wall_s"] / nr, 4)
+    fb1 = lat.new_field(0, hr.F64)
+    fx1 = lat.new_field(0, hr.F64)
+    fbytes = lat.field_bytes(0, hr.F64, 1)
+    fb1.copy_(fb[:fbytes])
+    r1 = _timed_cg(lat, fx1, fb1, m0, csw, hr.F32, reps=1)
+    line["mixed_fp32_1rhs"] = {k: r1[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
+    r64 = _timed_cg(lat, fx1, fb1, m0, csw, hr.F64, reps=1)
+    line["fp64_1rhs"] = {k: r64[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
+    line["per_rhs_speedup_vs_single_mixed"] = round(r1["wall_s"] / (r["wall_s"] / nr), 2)
+    line["per_rhs_speedup_vs_fp64"] = round(r64["wall_s"] / (r["wall_s"] / nr), 2)
+    out.append(line)
+    print(json.dumps(line), flush=True)
+    lat.close()
+    del fb, fx, fb1, fx1
+    torch.cuda.empty_cache()
+    # 64 lattices of mixed shape / N / representation, each to 1e-8
+    shapes = inputs.batch_shapes(2, 64)
+    lats, xs, bs = [], [], []
+    for k, (T, L, N, rep) in enumerate(shapes):
+        lt = _lattice(hr, inputs, torch, T, L, N, rep, 0.5, 0.0, seed=100 + k)
+        lats.append(lt)
+        bs.append(_pack_rhs(lt, inputs, torch, 200 + k, T, L, 1, hr.F64))
+        xs.append(lt.new_field(0, hr.F64))
+    batch = hr.Batch(lats)
+    batch.cg_solve(xs, bs, 0, [-0.3] * 64, 1e-8, inner_prec=hr.F32)   # warm-up (tuning, graph)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, st = batch.cg_solve(xs, bs, 0, [-0.3] * 64, 1e-8, inner_prec=hr.F32)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    per = []
+    for k, lt in enumerate(lats):
+        per.append(lt.cg_solve(xs[k], bs[k], 0, -0.3, 0.0, 1e-8, inner_prec=hr.F32, raise_on_error=False))
+    tp = time.perf_counter() - t0
+    vol = sum(T * L ** 3 for (T, L, N, rep) in shapes)
+    its = sum(s_["iterations"] for s_ in st)
+    line = {"suite": "64 lattices (8^4 .. 16^3x32, N 2..6, mixed reps) CG to 1e-8", "status": rc,
+            "sites": vol, "batched_s": round(tb, 4), "per_lattice_s": round(tp, 4),
+            "batched_speedup": round(tp / tb, 2),
+            "max_true_residual": max(s_["true_residual"] for s_ in st),
+            "iterations_sum": its, "site_iterations_per_s_batched": round(sum(
+                (T * L ** 3 // 2) * s_["iterations"] for (T, L, N, rep), s_ in zip(shapes, st)) / tb, 1)}
+    out.append(line)
+    print(json.dumps(line), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +342,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--suite", action="store_true", help="measure the other workloads instead of the bench line")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
     ap.add_argument("--L", type=int, default=WORKLOAD["L"], help="space extent (profiling runs only)")
     args = ap.parse_args()
@@ -197,6 +350,9 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.suite:
+        run_suite(args)
         return
 
     import torch
@@ -257,14 +413,10 @@ def main():
         dist.barrier()
     wall = time.perf_counter() - t_wall
     lat.synchronize()
-    ms_step = float(np.mean(ms32))
-    if dist:
-        tt = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = job_timing(float(np.mean(ms32)), world, dist, device="cuda")
     sites = lat.Vh
     b32 = bytes_per_even_site(N, rep, 4) * sites
-    gbs = world * b32 / (ms_step * 1e-3) / 1e9
+    gbs = job_value(b32, world, ms_step)
 
     # FP64 Dhat (FP64-ALU bound on this part)
     for _ in range(3):

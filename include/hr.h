@@ -215,9 +215,45 @@ int hr_norm2_static(const void *x, int64_t half_volume, int d, int parity, int p
 int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
                 const hr_cg_params *params, hr_cg_stats *stats);
 
+/* ---- many small lattices in one solve ----------------------------------- */
+
+typedef struct hr_batch hr_batch;
+
+/* Group n lattices (each created, links loaded, csw = 0; any mix of T, L, N,
+ * representation) for batched operator applications and solves.  The
+ * lattices must outlive the batch.  Lattices of equal (d_R, real links) form a
+ * class; each class runs one persistent multi-lattice launch per hopping
+ * stage, so a batched Dhat costs 2 x (number of classes) launches however
+ * many lattices there are (kernel-call overhead at small volumes, Sec. 3.1.1).
+ * Errors: HR_ERR_STATE (links missing), HR_ERR_UNSUPPORTED (clover). */
+int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out);
+int hr_batch_destroy(hr_batch *batch);
+/* Stream the batch's work is ordered after (default: the first lattice's). */
+int hr_batch_set_stream(hr_batch *batch, void *cuda_stream);
+
+/* out[i] = Dhat_p in[i] (or its adjoint) on lattice i, parity EVEN or ODD,
+ * bare mass m0[i] (host array); internal single-parity fields of precision
+ * prec, one rhs each.  The first call per precision times each class's
+ * launch shapes (outside stream capture). */
+int hr_batch_dphi(hr_batch *batch, void *const *out, const void *const *in, int parity, const double *m0,
+                  int prec, int dagger);
+
+/* Solve (Dhat_p^+ Dhat_p) x[i] = b[i] on every lattice to a true FP64
+ * relative residual params->tol per lattice (x, b: FP64 internal fields;
+ * x overwritten).  params->inner_prec HR_F32 or HR_F16: the inner CG of all
+ * lattices runs in lock step as one CUDA graph per chunk of
+ * params->check_every iterations; converged lattices are frozen on the device
+ * and skipped; FP64 defect correction per lattice between chunks.
+ * stats[i] (n entries) receives each lattice's iterations and residual.
+ * Synchronous.  Errors as hr_cg_solve. */
+int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int parity, const double *m0,
+                      const hr_cg_params *params, hr_cg_stats *stats);
+
 /* The hopping-kernel launch shape the autotuner chose for this lattice at
- * (prec, nrhs, clover): split_g * 1000 + threads per block (split_g = 0: one
- * site per thread; G > 0: G threads per site), or -1 if not tuned yet.  The
+ * (prec, nrhs, clover): regs * 10000 + split_g * 1000 + threads per block
+ * (split_g = 0: one site per thread with register budget regs = 0 compiler's
+ * choice, 1 up to ~170, 2 at most ~85 registers; G > 0: G threads per site),
+ * or -1 if not tuned yet.  The
  * first hr_dphi / hr_cg_solve call for a new shape key times the candidate
  * shapes on the caller's stream (make it outside any stream capture). */
 int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover);

@@ -1,0 +1,589 @@
+// Many independent lattices (uneven volume, N and representation) solved
+// together: the batched operator and CG (SURVEY workload of 64 small
+// lattices; the paper notes that at small volumes kernel-call overhead
+// dominates, Sec. 3.1.1 and Sec. 3.2).
+//
+// Lattices are grouped into classes of equal (d_R, real links); each class
+// runs one persistent multi-lattice hop launch per hopping stage over a work
+// list of (lattice, tile) items, each lattice bringing its own descriptor.
+// So one batched Dhat is 2 x (number of classes) launches whatever the number
+// of lattices.  The CG vector updates and reductions are single launches over
+// all lattices too, with one reduction slot (alpha, beta, |r|^2) per lattice.
+// The whole inner iteration (4 x classes hop launches + 3 BLAS launches) is
+// captured once into a CUDA graph and replayed in chunks; a lattice whose CG
+// has converged sets its frozen flag and its tiles are skipped by the hop and
+// update kernels while the others continue.  The FP64 outer defect correction
+// (true residual, rescaling, x update) runs per lattice between chunks.
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <math.h>
+#include <string.h>
+#include <vector>
+
+#include "blas_dev.cuh"
+#include "hop.cuh"
+
+namespace {
+
+struct BLat {         // per-lattice view for the batched vector kernels
+  char *x, *r;        // inner solution and residual (FP32)
+  char *p, *Ap, *t;   // operator fields (inner precision)
+  int64_t Vh;
+  int d, nblk;
+};
+
+struct BClass {
+  int d, is_real;
+  HopShape sh;
+  std::vector<int> members;
+  int2 *items;  // device work list (lattice index, tile)
+  int nitems;
+};
+
+enum { B_RR0 = 0, B_RR1, B_PAP, B_ALPHA, B_BETA, B_STOP, B_A, B_B, B_OUT, B_NS };
+
+int launch_multi(int prec, const BClass &c, const HopK *descs, const int *frozen, cudaStream_t s) {
+  switch (prec) {
+    case HR_F64: return hr_launch_hop_multi_f64(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
+    case HR_F32: return hr_launch_hop_multi_f32(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
+    case HR_F16: return hr_launch_hop_multi_f16(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
+  }
+  return HR_ERR_ARG;
+}
+
+template <int P>
+__global__ void bnorm2_kernel(const BLat *bl, const int2 *items, RedArgs red, int finish, const int *frozen) {
+  const int2 it = items[blockIdx.x];
+  const BLat L = bl[it.x];
+  double acc = 0.0;
+  if (!(frozen && frozen[it.x]))
+    acc = norm2_sites<P>(L.t, L.Vh, L.d, (int64_t)it.y * blockDim.x + threadIdx.x, (int64_t)L.nblk * blockDim.x);
+  reduce_publish(acc, red, finish, it.x, it.y, L.nblk);
+}
+
+template <int PR, int PP>
+__global__ void bcg_xr_kernel(const BLat *bl, const int2 *items, RedArgs red) {
+  typedef typename PT<PR>::A AR;
+  const int2 it = items[blockIdx.x];
+  const BLat L = bl[it.x];
+  const AR al = (AR)red.alpha[it.x];
+  double acc = 0.0;
+  if (al != (AR)0)
+    acc = cg_xr_sites<PR, PP>(L.x, L.r, L.p, L.Ap, L.Vh, L.d, al, (int64_t)it.y * blockDim.x + threadIdx.x,
+                              (int64_t)L.nblk * blockDim.x);
+  reduce_publish(acc, red, RED_BETA, it.x, it.y, L.nblk);
+}
+
+template <int PR, int PP>
+__global__ void bcg_p_kernel(const BLat *bl, const int2 *items, const double *beta, const double *alpha) {
+  const int2 it = items[blockIdx.x];
+  if (alpha[it.x] == 0.0) return;
+  const BLat L = bl[it.x];
+  cg_p_sites<PR, PP>(L.r, L.p, L.Vh, L.d, (typename PT<PP>::A)beta[it.x], (int64_t)it.y * blockDim.x + threadIdx.x,
+                     (int64_t)L.nblk * blockDim.x);
+}
+
+}  // namespace
+
+struct hr_batch {
+  int n;
+  std::vector<hr_lattice *> lats;
+  std::vector<BClass> cls;
+  cudaStream_t stream;  // caller's stream
+  cudaStream_t s;       // internal stream (capturable)
+  HopK *d_desc;         // [4 stages][n]
+  HopK *h_desc;         // pinned staging
+  BLat *d_blat;
+  BLat *h_blat;
+  int2 *d_bitems;
+  int nbitems;
+  double *scal;         // [B_NS][n]
+  double *host;         // pinned mirror
+  int *iters, *frozen, *err;
+  double *partials;
+  unsigned *count;
+  int tuned_prec;       // precision the class shapes were tuned for (-1: none)
+};
+
+static double *BS(hr_batch *b, int k) { return b->scal + (size_t)k * b->n; }
+
+static int build_items(BClass &c, const std::vector<hr_lattice *> &lats) {
+  const int tile = c.sh.split_g ? 128 / c.sh.split_g : c.sh.bs;
+  std::vector<int2> items;
+  for (int li : c.members) {
+    const int64_t nt = (lats[li]->Vh + tile - 1) / tile;
+    for (int64_t t = 0; t < nt; ++t) items.push_back(make_int2(li, (int)t));
+  }
+  cudaFree(c.items);
+  c.items = nullptr;
+  c.nitems = (int)items.size();
+  HR_CUDA(cudaMalloc(&c.items, sizeof(int2) * std::max<size_t>(1, items.size())));
+  HR_CUDA(cudaMemcpy(c.items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  return HR_OK;
+}
+
+extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
+  if (!out || !lats || n < 1 || n > 4096) return HR_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!lats[i]) return HR_ERR_ARG;
+    if (!lats[i]->have_links) return HR_ERR_STATE;
+    if (lats[i]->csw != 0.0) return HR_ERR_UNSUPPORTED;
+  }
+  hr_batch *b = new hr_batch();
+  b->n = n;
+  b->lats.assign(lats, lats + n);
+  b->stream = lats[0]->stream;
+  b->tuned_prec = -1;
+  std::map<int, int> cidx;
+  for (int i = 0; i < n; ++i) {
+    const int key = lats[i]->d * 2 + lats[i]->is_real;
+    auto it = cidx.find(key);
+    if (it == cidx.end()) {
+      BClass c;
+      c.d = lats[i]->d;
+      c.is_real = lats[i]->is_real;
+      c.items = nullptr;
+      c.nitems = 0;
+      HopShape shapes[HR_MAX_SHAPES];
+      if (hr_hop_shapes(c.d, c.is_real, HR_F32, 0, shapes) < 1) {
+        delete b;
+        return HR_ERR_UNSUPPORTED;
+      }
+      c.sh = shapes[0];
+      cidx[key] = (int)b->cls.size();
+      b->cls.push_back(c);
+      it = cidx.find(key);
+    }
+    b->cls[it->second].members.push_back(i);
+  }
+  int rc = HR_OK;
+  for (auto &c : b->cls)
+    if (rc == HR_OK) rc = build_items(c, b->lats);
+  std::vector<int2> bitems;
+  for (int i = 0; i < n; ++i) {
+    const int nblk = hr_blas_blocks(lats[i]->Vh);
+    for (int k = 0; k < nblk; ++k) bitems.push_back(make_int2(i, k));
+  }
+  b->nbitems = (int)bitems.size();
+  auto A = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == HR_OK) {
+      hr_note_cuda_error(e, "hr_batch_create", __FILE__, __LINE__);
+      rc = HR_ERR_CUDA;
+    }
+  };
+  A(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+  A(cudaMalloc(&b->d_desc, sizeof(HopK) * 4 * n));
+  A(cudaMallocHost(&b->h_desc, sizeof(HopK) * 4 * n));
+  A(cudaMalloc(&b->d_blat, sizeof(BLat) * n));
+  A(cudaMallocHost(&b->h_blat, sizeof(BLat) * n));
+  A(cudaMalloc(&b->d_bitems, sizeof(int2) * bitems.size()));
+  if (rc == HR_OK) A(cudaMemcpy(b->d_bitems, bitems.data(), sizeof(int2) * bitems.size(), cudaMemcpyHostToDevice));
+  A(cudaMalloc(&b->scal, sizeof(double) * B_NS * n));
+  A(cudaMallocHost(&b->host, sizeof(double) * B_NS * n));
+  A(cudaMalloc(&b->iters, sizeof(int) * n));
+  A(cudaMalloc(&b->frozen, sizeof(int) * n));
+  A(cudaMalloc(&b->err, sizeof(int)));
+  A(cudaMalloc(&b->partials, sizeof(double) * 2 * HR_RED_MAXBLK * n));
+  A(cudaMalloc(&b->count, sizeof(unsigned) * n));
+  if (rc == HR_OK) {
+    A(cudaMemset(b->count, 0, sizeof(unsigned) * n));
+    A(cudaMemset(b->err, 0, sizeof(int)));
+    A(cudaMemset(b->frozen, 0, sizeof(int) * n));
+    A(cudaMemset(b->scal, 0, sizeof(double) * B_NS * n));
+  }
+  if (rc != HR_OK) {
+    hr_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return HR_OK;
+}
+
+extern "C" int hr_batch_destroy(hr_batch *b) {
+  if (!b) return HR_ERR_ARG;
+  if (b->s) {
+    cudaStreamSynchronize(b->s);
+    cudaStreamDestroy(b->s);
+  }
+  for (auto &c : b->cls) cudaFree(c.items);
+  cudaFree(b->d_desc);
+  cudaFreeHost(b->h_desc);
+  cudaFree(b->d_blat);
+  cudaFreeHost(b->h_blat);
+  cudaFree(b->d_bitems);
+  cudaFree(b->scal);
+  cudaFreeHost(b->host);
+  cudaFree(b->iters);
+  cudaFree(b->frozen);
+  cudaFree(b->err);
+  cudaFree(b->partials);
+  cudaFree(b->count);
+  delete b;
+  return HR_OK;
+}
+
+extern "C" int hr_batch_set_stream(hr_batch *b, void *stream) {
+  if (!b) return HR_ERR_ARG;
+  b->stream = (cudaStream_t)stream;
+  return HR_OK;
+}
+
+// Descriptors of the two hopping stages of Dhat_p (or its adjoint) for every
+// lattice: stage 0: tmp_q = coef0 H in (A_qq^{-1} = 1/(4+m0)); stage 1:
+// out = (4+m0) in + 1/2 H tmp_q.  Written to h_desc[slot * n + lattice].
+static int fill_desc(hr_batch *b, int slot0, int prec, void *const *out, const void *const *in, int parity,
+                     const double *m0, int dagger) {
+  for (int i = 0; i < b->n; ++i) {
+    hr_lattice *lat = b->lats[i];
+    const size_t fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
+    HR_TRY(hr_ensure_tmp(lat, fb));
+    const double diag = 4.0 + m0[i];
+    HopArgs a;
+    memset(&a, 0, sizeof(a));
+    a.links = lat->links[prec];
+    a.dagger = dagger;
+    a.nrhs = 1;
+    a.field_stride = fb;
+    a.out = lat->tmp;
+    a.in = in[i];
+    a.out_parity = 1 - parity;
+    a.mode = HOP_SCALED;
+    a.coef = -0.5 / diag;
+    b->h_desc[(size_t)slot0 * b->n + i] = make_hopk(lat, a);
+    a.out = out[i];
+    a.in = lat->tmp;
+    a.self = in[i];
+    a.out_parity = parity;
+    a.mode = HOP_SELF;
+    a.coef = 0.5;
+    a.diag = diag;
+    b->h_desc[(size_t)(slot0 + 1) * b->n + i] = make_hopk(lat, a);
+  }
+  return HR_OK;
+}
+
+// Pick each class's launch shape by timing its candidates on stage 0 of the
+// uploaded descriptors (persistent multi-lattice launches).
+static int tune_classes(hr_batch *b, int prec, cudaStream_t s) {
+  if (b->tuned_prec == prec) return HR_OK;
+  cudaEvent_t e0, e1;
+  HR_CUDA(cudaEventCreate(&e0));
+  HR_CUDA(cudaEventCreate(&e1));
+  for (auto &c : b->cls) {
+    HopShape shapes[HR_MAX_SHAPES];
+    const int ns = hr_hop_shapes(c.d, c.is_real, prec, 0, shapes);
+    float best = 1e30f;
+    HopShape bs = shapes[0];
+    for (int k = 0; k < ns; ++k) {
+      c.sh = shapes[k];
+      HR_TRY(build_items(c, b->lats));
+      HR_TRY(launch_multi(prec, c, b->d_desc, nullptr, s));
+      HR_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) HR_TRY(launch_multi(prec, c, b->d_desc, nullptr, s));
+      HR_CUDA(cudaEventRecord(e1, s));
+      HR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      HR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bs = shapes[k];
+      }
+    }
+    c.sh = bs;
+    HR_TRY(build_items(c, b->lats));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tuned_prec = prec;
+  return HR_OK;
+}
+
+// launches of one batched Dhat (stages slot0, slot0+1 of d_desc)
+static int batch_dhat(hr_batch *b, int prec, int slot0, const int *frozen, cudaStream_t s) {
+  for (const auto &c : b->cls) HR_TRY(launch_multi(prec, c, b->d_desc + (size_t)slot0 * b->n, frozen, s));
+  for (const auto &c : b->cls) HR_TRY(launch_multi(prec, c, b->d_desc + (size_t)(slot0 + 1) * b->n, frozen, s));
+  return HR_OK;
+}
+
+extern "C" int hr_batch_dphi(hr_batch *b, void *const *out, const void *const *in, int parity, const double *m0,
+                             int prec, int dagger) {
+  if (!b || !out || !in || !m0 || (parity != HR_EVEN && parity != HR_ODD) || prec < HR_F64 || prec > HR_F16)
+    return HR_ERR_ARG;
+  for (int i = 0; i < b->n; ++i)
+    if (!out[i] || !in[i] || out[i] == in[i]) return HR_ERR_ARG;
+  HR_TRY(fill_desc(b, 0, prec, out, in, parity, m0, dagger));
+  HR_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(HopK) * 2 * b->n, cudaMemcpyHostToDevice, b->stream));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HR_CUDA(cudaStreamIsCapturing(b->stream, &cap));
+  if (cap == cudaStreamCaptureStatusNone) HR_TRY(tune_classes(b, prec, b->stream));
+  HR_TRY(batch_dhat(b, prec, 0, nullptr, b->stream));
+  for (auto *lat : b->lats) lat->hop_launches += 2;
+  return HR_OK;
+}
+
+// --------------------------------------------------------------- batched CG
+extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const *bsrc, int parity, const double *m0,
+                                 const hr_cg_params *prm, hr_cg_stats *stats) {
+  if (!b || !x || !bsrc || !m0 || !prm || (parity != HR_EVEN && parity != HR_ODD)) return HR_ERR_ARG;
+  if (prm->tol <= 0.0 || prm->inner_prec < HR_F32 || prm->inner_prec > HR_F16) return HR_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  const int n = b->n, lo = prm->inner_prec;
+  const int check_every = std::max(2, (prm->check_every > 0 ? prm->check_every : 10) & ~1);
+  const int maxit = prm->maxit > 0 ? prm->maxit : 100000;
+  const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 1e-2);
+  cudaStream_t s = b->s;
+  // order after the caller's stream
+  cudaEvent_t ev;
+  HR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HR_CUDA(cudaEventRecord(ev, b->stream));
+  HR_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  // workspaces and per-lattice descriptors
+  std::vector<void *> pl(n), Apl(n), tl(n);
+  for (int i = 0; i < n; ++i) {
+    hr_lattice *lat = b->lats[i];
+    HR_TRY(hr_cg_workspace(lat, HR_F64, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F64)));
+    HR_TRY(hr_cg_workspace(lat, HR_F32, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F32)));
+    if (lo == HR_F16) HR_TRY(hr_cg_workspace(lat, HR_F16, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F16)));
+    HR_TRY(hr_red_scratch(lat, 1));
+    HR_TRY(hr_ensure_tmp(lat, hr_spinor_field_bytes(lat->Vh, lat->d, HR_F64)));
+    pl[i] = hr_cg_field(lat, lo, 1);
+    Apl[i] = hr_cg_field(lat, lo, 2);
+    tl[i] = hr_cg_field(lat, lo, 3);
+    BLat &L = b->h_blat[i];
+    L.x = (char *)hr_cg_field(lat, HR_F32, 4);
+    L.r = (char *)hr_cg_field(lat, HR_F32, 0);
+    L.p = (char *)pl[i];
+    L.Ap = (char *)Apl[i];
+    L.t = (char *)tl[i];
+    L.Vh = lat->Vh;
+    L.d = lat->d;
+    L.nblk = hr_blas_blocks(lat->Vh);
+  }
+  HR_TRY(fill_desc(b, 0, lo, tl.data(), (const void *const *)pl.data(), parity, m0, 0));   // t = Dhat p
+  HR_TRY(fill_desc(b, 2, lo, Apl.data(), (const void *const *)tl.data(), parity, m0, 1));  // Ap = Dhat^+ t
+  HR_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(HopK) * 4 * n, cudaMemcpyHostToDevice, s));
+  HR_CUDA(cudaMemcpyAsync(b->d_blat, b->h_blat, sizeof(BLat) * n, cudaMemcpyHostToDevice, s));
+  HR_TRY(tune_classes(b, lo, s));
+  HR_CUDA(cudaMemsetAsync(b->iters, 0, sizeof(int) * n, s));
+
+  RedArgs red;
+  memset(&red, 0, sizeof(red));
+  red.partials = b->partials;
+  red.count = b->count;
+  red.err = b->err;
+  red.stop = BS(b, B_STOP);
+  red.iters = b->iters;
+  red.frozen = b->frozen;
+
+  // capture one chunk of check_every inner iterations
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  HR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = HR_OK;
+  const dim3 bgrid(b->nbitems);
+  for (int k = 0; k < check_every && rc == HR_OK; ++k) {
+    double *rr = BS(b, (k & 1) ? B_RR1 : B_RR0), *rr_next = BS(b, (k & 1) ? B_RR0 : B_RR1);
+    rc = batch_dhat(b, lo, 0, b->frozen, s);
+    if (rc != HR_OK) break;
+    RedArgs ra = red;
+    ra.out = BS(b, B_PAP);
+    ra.rr = rr;
+    ra.alpha = BS(b, B_ALPHA);
+    if (lo == HR_F32) bnorm2_kernel<1><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, ra, RED_ALPHA, b->frozen);
+    else bnorm2_kernel<2><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, ra, RED_ALPHA, b->frozen);
+    rc = batch_dhat(b, lo, 2, b->frozen, s);
+    if (rc != HR_OK) break;
+    RedArgs rb = red;
+    rb.out = BS(b, B_OUT);
+    rb.rr = rr;
+    rb.rr_next = rr_next;
+    rb.alpha = BS(b, B_ALPHA);
+    rb.beta = BS(b, B_BETA);
+    if (lo == HR_F32) {
+      bcg_xr_kernel<1, 1><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, rb);
+      bcg_p_kernel<1, 1><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, BS(b, B_BETA), BS(b, B_ALPHA));
+    } else {
+      bcg_xr_kernel<1, 2><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, rb);
+      bcg_p_kernel<1, 2><<<bgrid, 256, 0, s>>>(b->d_blat, b->d_bitems, BS(b, B_BETA), BS(b, B_ALPHA));
+    }
+  }
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (rc != HR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  HR_CUDA(ce);
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  HR_CUDA(ce);
+
+  // FP64 outer loop
+  std::vector<double> bn2(n), rn2(n), hv(n);
+  std::vector<int> active(n, 1);
+  auto set = [&](int which, const std::vector<double> &v) -> int {
+    HR_CUDA(cudaMemcpyAsync(BS(b, which), v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    HR_CUDA(cudaStreamSynchronize(s));
+    return HR_OK;
+  };
+  // per-lattice FP64 helpers (slot 0 of each lattice's own reduction scratch)
+  auto lat_red = [&](hr_lattice *lat) {
+    RedArgs r;
+    memset(&r, 0, sizeof(r));
+    r.partials = lat->red_partials;
+    r.count = lat->red_count;
+    r.out = lat->red_out;
+    r.err = lat->dev_err;
+    return r;
+  };
+  auto fd = [&](hr_lattice *lat, int prec) {
+    FieldDesc f;
+    f.Vh = lat->Vh;
+    f.d = lat->d;
+    f.fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
+    f.nsub = 1;
+    return f;
+  };
+  // scalar constants on the device: a, b per lattice in B_A / B_B
+  std::vector<double> va(n), vb(n);
+  auto residual = [&](int i) -> int {  // r = b - M x (FP64) -> rn2[i]
+    hr_lattice *lat = b->lats[i];
+    void *r = hr_cg_field(lat, HR_F64, 0), *Ap = hr_cg_field(lat, HR_F64, 2), *t = hr_cg_field(lat, HR_F64, 3);
+    HR_TRY(hr_dphi_impl(lat, t, x[i], parity, m0[i], 0.0, HR_F64, 1, 0, s));
+    HR_TRY(hr_dphi_impl(lat, Ap, t, parity, m0[i], 0.0, HR_F64, 1, 1, s));
+    const FieldDesc f = fd(lat, HR_F64);
+    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, bsrc[i], r, f, f, 1, BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
+    return HR_OK;
+  };
+  // x = 0; r = b; |b|^2
+  for (int i = 0; i < n; ++i) {
+    va[i] = 1.0;
+    vb[i] = 0.0;
+  }
+  HR_TRY(set(B_A, va));
+  HR_TRY(set(B_B, vb));
+  for (int i = 0; i < n; ++i) {
+    hr_lattice *lat = b->lats[i];
+    const FieldDesc f = fd(lat, HR_F64);
+    HR_CUDA(cudaMemsetAsync(x[i], 0, f.fb, s));
+    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, bsrc[i], hr_cg_field(lat, HR_F64, 0), f, f, 1, BS(b, B_A) + i,
+                         BS(b, B_B) + i, lat_red(lat), 1, s));
+    HR_CUDA(cudaMemcpyAsync(&b->host[i], lat->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  HR_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) rn2[i] = bn2[i] = b->host[i];
+
+  int status = HR_OK, iters = 0, outer = 0;
+  const double tol2 = prm->tol * prm->tol;
+  while (true) {
+    int nact = 0;
+    for (int i = 0; i < n; ++i) {
+      active[i] = !(rn2[i] <= tol2 * bn2[i]);
+      nact += active[i];
+    }
+    if (nact == 0) break;
+    if (iters >= maxit || outer >= 200) {
+      status = HR_ERR_NOT_CONVERGED;
+      break;
+    }
+    // rl = r / |r|, pl = rl, xl = 0 on active lattices; stop and rr per lattice
+    std::vector<double> stop(n), rr(n), inv(n), one(n, 1.0), zero(n, 0.0);
+    std::vector<int> frz(n);
+    for (int i = 0; i < n; ++i) {
+      const double rn = sqrt(rn2[i]);
+      inv[i] = (active[i] && rn > 0.0) ? 1.0 / rn : 0.0;
+      double tgt = prm->tol * sqrt(bn2[i]) / (2.0 * (rn > 0.0 ? rn : 1.0));
+      if (tgt < inner_tol) tgt = inner_tol;
+      stop[i] = active[i] ? tgt * tgt : 1e300;
+      rr[i] = active[i] ? 1.0 : 0.0;
+      frz[i] = active[i] ? 0 : 1;
+    }
+    HR_TRY(set(B_A, inv));
+    HR_TRY(set(B_B, zero));
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      hr_lattice *lat = b->lats[i];
+      HR_TRY(hr_blas_axpby(HR_F64, HR_F32, hr_cg_field(lat, HR_F64, 0), b->h_blat[i].r, fd(lat, HR_F64),
+                           fd(lat, HR_F32), 1, BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
+    }
+    HR_TRY(set(B_A, one));
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      hr_lattice *lat = b->lats[i];
+      HR_TRY(hr_blas_axpby(HR_F32, lo, b->h_blat[i].r, pl[i], fd(lat, HR_F32), fd(lat, lo), 1, BS(b, B_A) + i,
+                           BS(b, B_B) + i, lat_red(lat), 0, s));
+      HR_CUDA(cudaMemsetAsync(b->h_blat[i].x, 0, fd(lat, HR_F32).fb, s));
+    }
+    HR_TRY(set(B_STOP, stop));
+    HR_TRY(set(B_RR0, rr));
+    HR_CUDA(cudaMemcpyAsync(b->frozen, frz.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    HR_CUDA(cudaStreamSynchronize(s));
+    // inner chunks
+    int done = 0;
+    while (iters + done < maxit) {
+      HR_CUDA(cudaGraphLaunch(exec, s));
+      done += check_every;
+      HR_CUDA(cudaMemcpyAsync(frz.data(), b->frozen, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+      HR_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int i = 0; i < n; ++i) all = all && frz[i];
+      if (all) break;
+    }
+    iters += done;
+    ++outer;
+    int herr = 0;
+    HR_CUDA(cudaMemcpy(&herr, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+      HR_CUDA(cudaMemset(b->err, 0, sizeof(int)));
+      status = HR_ERR_BREAKDOWN;
+      break;
+    }
+    // x += |r| xl; r = b - M x
+    std::vector<double> rnv(n);
+    for (int i = 0; i < n; ++i) rnv[i] = sqrt(rn2[i]);
+    HR_TRY(set(B_A, rnv));
+    HR_TRY(set(B_B, one));
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      hr_lattice *lat = b->lats[i];
+      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, b->h_blat[i].x, x[i], fd(lat, HR_F32), fd(lat, HR_F64), 1,
+                           BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
+    }
+    // r = 1*b + 0*r, then r = -1*Ap + 1*r with |r|^2
+    HR_TRY(set(B_A, one));
+    HR_TRY(set(B_B, zero));
+    for (int i = 0; i < n; ++i)
+      if (active[i]) HR_TRY(residual(i));
+    std::vector<double> mone(n, -1.0);
+    HR_TRY(set(B_A, mone));
+    HR_TRY(set(B_B, one));
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      hr_lattice *lat = b->lats[i];
+      const FieldDesc f = fd(lat, HR_F64);
+      HR_TRY(hr_blas_axpby(HR_F64, HR_F64, hr_cg_field(lat, HR_F64, 2), hr_cg_field(lat, HR_F64, 0), f, f, 1,
+                           BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 1, s));
+      HR_CUDA(cudaMemcpyAsync(&b->host[i], lat->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    HR_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+      if (active[i]) rn2[i] = b->host[i];
+  }
+  cudaGraphExecDestroy(exec);
+  HR_CUDA(cudaStreamSynchronize(s));
+  HR_CUDA(cudaEventDestroy(ev));
+  if (stats) {
+    std::vector<int> it(n);
+    HR_CUDA(cudaMemcpy(it.data(), b->iters, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; ++i) {
+      stats[i].iterations = it[i];
+      stats[i].outer_steps = outer;
+      stats[i].true_residual = bn2[i] > 0.0 ? sqrt(rn2[i] / bn2[i]) : 0.0;
+      stats[i].seconds = secs;
+      stats[i].hop_launches = 0.0;
+    }
+  }
+  return status;
+}

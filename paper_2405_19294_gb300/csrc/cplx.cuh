@@ -5,10 +5,6 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
-#ifndef HR_LINK_STREAMING
-#define HR_LINK_STREAMING 0   // 1: links are read with evict-first (streaming) loads
-#endif
-
 template <typename R>
 struct cx {
   R x, y;
@@ -72,11 +68,7 @@ __device__ __forceinline__ cx<double> ld2<0>(const void *base, int64_t idx) {
 }
 template <>
 __device__ __forceinline__ cx<float> ld2<1>(const void *base, int64_t idx) {
-#if HR_LINK_STREAMING
-  float2 v = __ldcs(reinterpret_cast<const float2 *>(base) + idx);
-#else
   float2 v = __ldg(reinterpret_cast<const float2 *>(base) + idx);
-#endif
   return mk(v.x, v.y);
 }
 template <>

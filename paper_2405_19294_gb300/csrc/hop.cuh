@@ -294,8 +294,11 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
   }
 }
 
-template <int D, bool REAL, int P>
-__global__ void __launch_bounds__(256) hop_kernel(HopK k) {
+// Register budget variants (the autotuner picks one with the block size):
+// MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
+// loads in flight per thread) and 64 x 12 (at most ~85 registers: more warps).
+template <int D, bool REAL, int P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k) {
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
@@ -341,27 +344,33 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   return k;
 }
 
+template <int D, bool REAL, int P>
+static void launch_site(const HopK &k, dim3 grid, int bs, int variant, cudaStream_t st) {
+  if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k);
+  else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k);
+  else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k);
+}
+
 // Launch the site-per-thread kernel for (D, REAL) of precision P with `bs`
-// threads per block (32 ... 256; the autotuner picks it).
+// threads per block and register-budget variant 0/1/2 (the autotuner picks).
 template <int P>
-int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int bs) {
+int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int bs, int variant) {
   const HopK k = make_hopk(lat, a);
-  dim3 block(bs);
   dim3 grid((unsigned)(((lat->Vh + bs - 1) / bs) * a.nrhs));
   const int d = lat->d;
   if (lat->is_real) {
     switch (d) {
-      case 3: hop_kernel<3, true, P><<<grid, block, 0, st>>>(k); break;
-      case 8: hop_kernel<8, true, P><<<grid, block, 0, st>>>(k); break;
+      case 3: launch_site<3, true, P>(k, grid, bs, variant, st); break;
+      case 8: launch_site<8, true, P>(k, grid, bs, variant, st); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   } else {
     switch (d) {
-      case 2: hop_kernel<2, false, P><<<grid, block, 0, st>>>(k); break;
-      case 3: hop_kernel<3, false, P><<<grid, block, 0, st>>>(k); break;
-      case 4: hop_kernel<4, false, P><<<grid, block, 0, st>>>(k); break;
-      case 5: hop_kernel<5, false, P><<<grid, block, 0, st>>>(k); break;
-      case 6: hop_kernel<6, false, P><<<grid, block, 0, st>>>(k); break;
+      case 2: launch_site<2, false, P>(k, grid, bs, variant, st); break;
+      case 3: launch_site<3, false, P>(k, grid, bs, variant, st); break;
+      case 4: launch_site<4, false, P>(k, grid, bs, variant, st); break;
+      case 5: launch_site<5, false, P>(k, grid, bs, variant, st); break;
+      case 6: launch_site<6, false, P>(k, grid, bs, variant, st); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   }

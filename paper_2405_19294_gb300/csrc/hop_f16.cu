@@ -5,7 +5,7 @@
 
 int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh) {
   const int d = lat->d;
-  if (sh.split_g == 0) return hop_dispatch<2>(lat, a, s, sh.bs);
+  if (sh.split_g == 0) return hop_dispatch<2>(lat, a, s, sh.bs, sh.regs);
   if (a.clover) return HR_ERR_UNSUPPORTED;
   const HopK k = make_hopk(lat, a);
   const int g = sh.split_g;

@@ -128,13 +128,16 @@ struct HopArgs {
 };
 
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
-// thread kernel with `bs` threads per block; split_g = G > 0 is the
-// colour-split kernel with G threads per site (128 threads per block).
+// thread kernel with `bs` threads per block and register-budget variant
+// `regs` (0: compiler's choice for 256 threads, 1: up to ~170 registers,
+// 2: at most ~85 registers); split_g = G > 0 is the colour-split kernel with
+// G threads per site (128 threads per block).
 struct HopShape {
   int split_g;
   int bs;
+  int regs;
 };
-#define HR_MAX_SHAPES 8
+#define HR_MAX_SHAPES 12
 
 // Candidate shapes for (d, real, precision); clover restricts to split_g = 0.
 int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out);

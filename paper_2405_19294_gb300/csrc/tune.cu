@@ -19,12 +19,20 @@
 #include "hr_internal.h"
 
 int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out) {
-  (void)prec;
   int n = 0;
   const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
   if (site) {
+    // compiler's register choice at 64 / 128 / 32 / 256 threads, then (not
+    // for FP64, which is ALU-bound) the high- and low-register budgets
     const int bss[4] = {64, 128, 32, 256};
-    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k]};
+    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0};
+    if (prec != HR_F64) {
+      out[n++] = HopShape{0, 32, 1};
+      out[n++] = HopShape{0, 64, 1};
+      out[n++] = HopShape{0, 128, 1};
+      out[n++] = HopShape{0, 32, 2};
+      out[n++] = HopShape{0, 64, 2};
+    }
   }
   if (!clover) {
     int gs[2] = {0, 0};
@@ -38,7 +46,7 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out) {
       if (d == 15 || d == 21) { gs[0] = 4; gs[1] = 8; }
     }
     for (int k = 0; k < 2; ++k)
-      if (gs[k]) out[n++] = HopShape{gs[k], 128};
+      if (gs[k]) out[n++] = HopShape{gs[k], 128, 0};
   }
   return n;
 }
@@ -111,7 +119,7 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 }
 
 // Report the tuned shape for the lattice's hop at (prec, nrhs, clover): returns
-// split_g * 1000 + block size, or -1 if that key has not been tuned yet.
+// regs * 10000 + split_g * 1000 + block size, or -1 if that key is not tuned yet.
 extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover) {
   if (!lat) return -1;
   HopArgs a;
@@ -121,15 +129,15 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_best.find(tune_key(lat, prec, a));
   if (it == g_best.end()) return -1;
-  return it->second.split_g * 1000 + it->second.bs;
+  return it->second.regs * 10000 + it->second.split_g * 1000 + it->second.bs;
 }
 
-// Candidate shapes of this lattice's hop, encoded split_g * 1000 + block size.
+// Candidate shapes of this lattice's hop, encoded regs * 10000 + split_g * 1000 + block size.
 extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clover, int *out, int max) {
   if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
-  for (int k = 0; k < n && k < max; ++k) out[k] = shapes[k].split_g * 1000 + shapes[k].bs;
+  for (int k = 0; k < n && k < max; ++k) out[k] = shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs;
   return n;
 }
 
@@ -140,7 +148,7 @@ extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
   for (int k = 0; k < n; ++k)
-    if (shapes[k].split_g * 1000 + shapes[k].bs == shape) {
+    if (shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
       HopArgs a;
       memset(&a, 0, sizeof(a));
       a.nrhs = nrhs;

@@ -65,6 +65,12 @@ _SIGS = {
     "hr_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "hr_hop_shape_candidates": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hr_set_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "hr_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
+    "hr_batch_destroy": (C.c_int, [_P]),
+    "hr_batch_set_stream": (C.c_int, [_P, _P]),
+    "hr_batch_dphi": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int]),
+    "hr_batch_cg_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double),
+                                    C.POINTER(hr_cg_params), C.POINTER(hr_cg_stats)]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -172,20 +178,20 @@ class Lattice:
                "hr_dphi")
 
     def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
-        """(threads per site group G or 0, threads per block) chosen by the autotuner, or None."""
+        """(G threads per site or 0, threads per block, register budget) chosen by the autotuner, or None."""
         v = _lib.hr_tuned_shape(self._h, prec, nrhs, int(clover))
-        return None if v < 0 else (v // 1000, v % 1000)
+        return None if v < 0 else ((v % 10000) // 1000, v % 1000, v // 10000)
 
     def shape_candidates(self, prec: int, clover: bool = False):
         buf = (C.c_int * 16)()
         n = _lib.hr_hop_shape_candidates(self._h, prec, int(clover), buf, 16)
         if n < 0:
             raise HrError(n, "hr_hop_shape_candidates")
-        return [(v // 1000, v % 1000) for v in buf[:n]]
+        return [((v % 10000) // 1000, v % 1000, v // 10000) for v in buf[:min(n, 16)]]
 
     def set_shape(self, prec: int, shape, nrhs: int = 1, clover: bool = False):
-        _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), shape[0] * 1000 + shape[1]),
-               "hr_set_tuned_shape")
+        code = shape[2] * 10000 + shape[0] * 1000 + shape[1]
+        _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), code), "hr_set_tuned_shape")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
         out = (C.c_double * nrhs)()
@@ -203,6 +209,50 @@ class Lattice:
         return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
                 "true_residual": st.true_residual, "seconds": st.seconds,
                 "hop_launches": st.hop_launches}
+
+
+class Batch:
+    """Many lattices solved together (one launch per representation class and stage)."""
+
+    def __init__(self, lattices):
+        import torch
+        self.lattices = list(lattices)
+        arr = (_P * len(self.lattices))(*[l._h for l in self.lattices])
+        h = _P()
+        _check(_lib.hr_batch_create(len(self.lattices), arr, C.byref(h)), "hr_batch_create")
+        self._h = h
+        _check(_lib.hr_batch_set_stream(h, C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "hr_batch_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, ts):
+        return (_P * len(ts))(*[_ptr(t) for t in ts])
+
+    def dphi(self, outs, ins, parity: int, m0s, prec: int, dagger: bool = False):
+        m = (C.c_double * len(m0s))(*m0s)
+        _check(_lib.hr_batch_dphi(self._h, self._ptrs(outs), self._ptrs(ins), parity, m, prec, int(dagger)),
+               "hr_batch_dphi")
+
+    def cg_solve(self, xs, bs, parity: int, m0s, tol: float, inner_prec: int = F32, inner_tol: float = 0.0,
+                 maxit: int = 100000, check_every: int = 10, raise_on_error: bool = True):
+        m = (C.c_double * len(m0s))(*m0s)
+        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, 1, check_every)
+        st = (hr_cg_stats * len(xs))()
+        rc = _lib.hr_batch_cg_solve(self._h, self._ptrs(xs), self._ptrs(bs), parity, m, C.byref(prm), st)
+        if rc != 0 and raise_on_error:
+            raise HrError(rc, "hr_batch_cg_solve")
+        return rc, [{"iterations": s.iterations, "outer_steps": s.outer_steps, "true_residual": s.true_residual,
+                     "seconds": s.seconds} for s in st]
 
 
 def lib_handle():
