@@ -232,13 +232,23 @@ def _timed_cg(lat, fx, fb, m0, csw, inner, nrhs=1, inner_tol=0.0, reps=2):
     return res
 
 
+def _warm(lat, prec, nrhs, m0, csw):
+    """One operator application per key so the autotuner runs outside the timed solves."""
+    fi = lat.new_field(0, prec, nrhs)
+    fo = lat.new_field(0, prec, nrhs)
+    lat.dphi(fo, fi, 0, m0, csw, prec, nrhs)
+    lat.dphi(fi, fo, 0, m0, csw, prec, nrhs, True)
+    lat.synchronize()
+
+
 def run_suite(args):
     """Measurements of the other workloads (one JSON line each; not the bench line)."""
     import torch
     from paper_2405_19294_gb300 import hr, inputs
     out = []
+    which = set(args.suite.split(","))
     # SU(2) adjoint and SU(4) antisymmetric on 24^3 x 48: mixed-precision CG
-    for N, rep in ((2, "adj"), (4, "asym")):
+    for N, rep in ((2, "adj"), (4, "asym")) if "c2" in which else ():
         T, L, m0 = 48, 24, -0.3
         lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
         fb = _pack_rhs(lat, inputs, torch, 1, T, L, 1, hr.F64)
@@ -278,9 +288,19 @@ def run_suite(args):
         lat.close()
         del fb, fx
         torch.cuda.empty_cache()
-    # SU(3) sextet with clover, 32^3 x 64, 12 right-hand sides
+    if "c3" in which:
+        out.append(_suite_c3(hr, inputs, torch))
+    if "c4" in which:
+        out.append(_suite_c4(hr, inputs, torch))
+    return out
+
+
+def _suite_c3(hr, inputs, torch):
+    """SU(3) sextet with clover, 32^3 x 64, 12 right-hand sides in one solve."""
     T, L, N, rep, m0, csw, nr = 64, 32, 3, "sym", -0.35, 1.0, 12
     lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, csw)
+    for prec, k in ((hr.F32, nr), (hr.F32, 1), (hr.F64, nr), (hr.F64, 1)):
+        _warm(lat, prec, k, m0, csw)
     fb = _pack_rhs(lat, inputs, torch, 1, T, L, nr, hr.F64)
     fx = lat.new_field(0, hr.F64, nr)
     line = {"suite": "SU(3) sym csw=1 32^3x64 12 rhs CG to 1e-10", "m0": m0}
@@ -297,12 +317,35 @@ def run_suite(args):
     line["fp64_1rhs"] = {k: r64[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
     line["per_rhs_speedup_vs_single_mixed"] = round(r1["wall_s"] / (r["wall_s"] / nr), 2)
     line["per_rhs_speedup_vs_fp64"] = round(r64["wall_s"] / (r["wall_s"] / nr), 2)
-    out.append(line)
+    # the operator alone: 12-rhs Dhat vs 12 single-rhs Dhat, FP32
+    fi = lat.new_field(0, hr.F32, nr)
+    fo = lat.new_field(0, hr.F32, nr)
+    st = torch.cuda.current_stream()
+    fbytes32 = lat.field_bytes(0, hr.F32, 1)
+    def _ev(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a_.elapsed_time(b_) for a_, b_ in ts]))
+    t_multi = _ev(lambda: lat.dphi(fo, fi, 0, m0, csw, hr.F32, nr))
+    t_single = _ev(lambda: [lat.dphi(fo[r * fbytes32:(r + 1) * fbytes32], fi[r * fbytes32:(r + 1) * fbytes32],
+                                     0, m0, csw, hr.F32, 1) for r in range(nr)])
+    line["dhat_ms_12rhs"] = round(t_multi, 3)
+    line["dhat_ms_12x1rhs"] = round(t_single, 3)
     print(json.dumps(line), flush=True)
     lat.close()
-    del fb, fx, fb1, fx1
+    del fb, fx, fb1, fx1, fi, fo
     torch.cuda.empty_cache()
-    # 64 lattices of mixed shape / N / representation, each to 1e-8
+    return line
+
+
+def _suite_c4(hr, inputs, torch):
+    """64 lattices of mixed shape / N / representation, each solved to 1e-8."""
     shapes = inputs.batch_shapes(2, 64)
     lats, xs, bs = [], [], []
     for k, (T, L, N, rep) in enumerate(shapes):
@@ -316,6 +359,9 @@ def run_suite(args):
     t0 = time.perf_counter()
     rc, st = batch.cg_solve(xs, bs, 0, [-0.3] * 64, 1e-8, inner_prec=hr.F32)
     tb = time.perf_counter() - t0
+    for k, lt in enumerate(lats):      # warm-up: tuning and graphs of the single-lattice path
+        lt.cg_solve(xs[k], bs[k], 0, -0.3, 0.0, 1e-8, inner_prec=hr.F32, raise_on_error=False)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     per = []
     for k, lt in enumerate(lats):
@@ -329,9 +375,9 @@ def run_suite(args):
             "max_true_residual": max(s_["true_residual"] for s_ in st),
             "iterations_sum": its, "site_iterations_per_s_batched": round(sum(
                 (T * L ** 3 // 2) * s_["iterations"] for (T, L, N, rep), s_ in zip(shapes, st)) / tb, 1)}
-    out.append(line)
     print(json.dumps(line), flush=True)
-    return out
+    batch.close()
+    return line
 
 
 def main():
@@ -342,7 +388,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", action="store_true", help="measure the other workloads instead of the bench line")
+    ap.add_argument("--suite", default="", help="comma list of c2,c3,c4: measure those workloads instead")
+    ap.add_argument("--shape", default="", help="pin the FP32 hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
     ap.add_argument("--L", type=int, default=WORKLOAD["L"], help="space extent (profiling runs only)")
     args = ap.parse_args()
@@ -380,6 +427,9 @@ def main():
     del psi
     src = src_host.cuda()
     stream = torch.cuda.current_stream()
+    if args.shape:
+        regs, g, bs = (int(v) for v in args.shape.split(","))
+        lat.set_shape(hr.F32, (g, bs, regs))
     fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
     fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
     for p in (hr.F64, hr.F32):
@@ -426,7 +476,12 @@ def main():
     b64 = bytes_per_even_site(N, rep, 8) * sites
     fl = flops_per_even_site(N, rep) * sites
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: the canonical FP64 source
+    # and result live in page-locked host memory; one DMA copy each way around
+    # pack -> Dhat -> unpack.  (The library can also read / write page-locked
+    # host memory in place -- only the parity's sites cross the host link -- but
+    # per-thread scattered reads over the host link measured slower than one
+    # bulk DMA copy of the whole field for this layout.)
     out_host = torch.empty_like(src_host).pin_memory()
     dev_in = torch.empty_like(src)
     dev_out = torch.zeros_like(src)

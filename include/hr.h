@@ -155,14 +155,18 @@ int hr_export_clover(hr_lattice *lat, double *A_dev, double m0, int inverse);
 
 /* ---- spinor fields ------------------------------------------------------ */
 
-/* Canonical FP64 spinors psi[nrhs][V][4][d] (device) -> internal field of
- * the given parity and precision (device).  Only sites of that parity are
- * read (both for FULL).  FP16 code: per site, scale = max |fp32(v)| over its
+/* Canonical FP64 spinors psi[nrhs][V][4][d] -> internal field of the given
+ * parity and precision (device).  Only sites of that parity are read (both
+ * for FULL).  `canonical` may be device memory or page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister / pinned torch tensors): the kernel then
+ * reads the host buffer directly through its mapped address, so only that
+ * parity's sites cross the host link; pageable host memory -> HR_ERR_ARG.  FP16 code: per site, scale = max |fp32(v)| over its
  * 8d reals, stored values fp16_rn(fp32(v) / scale) with IEEE division. */
 int hr_pack_spinor(hr_lattice *lat, void *internal, const double *canonical, int parity,
                    int prec, int nrhs);
 
-/* Internal field -> canonical FP64 spinors (device).  Sites of the other
+/* Internal field -> canonical FP64 spinors (device or page-locked host
+ * memory, written directly as for hr_pack_spinor).  Sites of the other
  * parity are left untouched (set to zero first if that matters). */
 int hr_unpack_spinor(hr_lattice *lat, double *canonical, const void *internal, int parity,
                      int prec, int nrhs);
@@ -250,17 +254,19 @@ int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int
                       const hr_cg_params *params, hr_cg_stats *stats);
 
 /* The hopping-kernel launch shape the autotuner chose for this lattice at
- * (prec, nrhs, clover): regs * 10000 + split_g * 1000 + threads per block
- * (split_g = 0: one site per thread with register budget regs = 0 compiler's
- * choice, 1 up to ~170, 2 at most ~85 registers; G > 0: G threads per site),
- * or -1 if not tuned yet.  The
+ * (prec, nrhs, clover): mrhs * 100000 + regs * 10000 + split_g * 1000 +
+ * threads per block.  mrhs = S > 0: the multi-right-hand-side kernel with S
+ * sites per block (links staged once per site for all right-hand sides);
+ * split_g = 0: one site per thread with register budget regs = 0 compiler's
+ * choice, 1 up to ~170, 2 at most ~85 registers; split_g = G > 0: G threads
+ * per site.  -1 if not tuned yet.  The
  * first hr_dphi / hr_cg_solve call for a new shape key times the candidate
  * shapes on the caller's stream (make it outside any stream capture). */
 int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover);
 
-/* The candidate shapes for this lattice at (prec, clover), encoded as above,
- * into out[0..max); returns how many exist (may exceed max) or an error. */
-int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clover, int *out, int max);
+/* The candidate shapes for this lattice at (prec, nrhs, clover), encoded as
+ * above, into out[0..max); returns how many exist (may exceed max) or an error. */
+int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs, int clover, int *out, int max);
 
 /* Pin the shape for (prec, nrhs, clover) instead of timing candidates
  * (reproducible runs, tests of every shape).  HR_ERR_ARG unless `shape` is

@@ -147,7 +147,7 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
       c.items = nullptr;
       c.nitems = 0;
       HopShape shapes[HR_MAX_SHAPES];
-      if (hr_hop_shapes(c.d, c.is_real, HR_F32, 0, shapes) < 1) {
+      if (hr_hop_shapes(c.d, c.is_real, HR_F32, 0, 0, shapes) < 1) {
         delete b;
         return HR_ERR_UNSUPPORTED;
       }
@@ -273,7 +273,7 @@ static int tune_classes(hr_batch *b, int prec, cudaStream_t s) {
   HR_CUDA(cudaEventCreate(&e1));
   for (auto &c : b->cls) {
     HopShape shapes[HR_MAX_SHAPES];
-    const int ns = hr_hop_shapes(c.d, c.is_real, prec, 0, shapes);
+    const int ns = hr_hop_shapes(c.d, c.is_real, prec, 0, 0, shapes);
     float best = 1e30f;
     HopShape bs = shapes[0];
     for (int k = 0; k < ns; ++k) {

@@ -132,15 +132,19 @@ struct HopArgs {
 // `regs` (0: compiler's choice for 256 threads, 1: up to ~170 registers,
 // 2: at most ~85 registers); split_g = G > 0 is the colour-split kernel with
 // G threads per site (128 threads per block).
+// mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
+// links staged once per site for all right-hand sides of the block).
 struct HopShape {
   int split_g;
   int bs;
   int regs;
+  int mrhs;
 };
-#define HR_MAX_SHAPES 12
+#define HR_MAX_SHAPES 16
 
-// Candidate shapes for (d, real, precision); clover restricts to split_g = 0.
-int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out);
+// Candidate shapes for (d, real, precision, several rhs); clover restricts to
+// split_g = 0.
+int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopShape *out);
 int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s);
 int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);

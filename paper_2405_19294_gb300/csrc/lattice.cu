@@ -251,11 +251,40 @@ __global__ void unpack_kernel(double *canon, const void *internal, PackK k) {
   }
 }
 
+// A canonical buffer may be device memory or page-locked (registered or
+// cudaHostAlloc'd) host memory; for the latter the kernels access it through
+// its mapped device address, so only the requested parity's sites cross the
+// host link (NVLink-C2C on GB300) and no staging copy is needed.  Pageable,
+// unregistered host memory is rejected (HR_ERR_ARG).
+static int resolve_canonical(const void *p, const void **dev) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_ARG;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *dev = p;
+    return HR_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return HR_OK;
+  }
+  return HR_ERR_ARG;
+}
+
 static int pack_common(hr_lattice *lat, void *internal, double *canon_w, const double *canon_r, int parity,
                        int prec, int nrhs, bool pack) {
   if (!lat || !internal || !(pack ? (const void *)canon_r : (const void *)canon_w) || nrhs < 1 ||
       prec < HR_F64 || prec > HR_F16 || parity < HR_EVEN || parity > HR_FULL)
     return HR_ERR_ARG;
+  {
+    const void *dev = nullptr;
+    HR_TRY(resolve_canonical(pack ? (const void *)canon_r : (const void *)canon_w, &dev));
+    if (pack) canon_r = (const double *)dev;
+    else canon_w = (double *)dev;
+  }
   const size_t fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
   PackK k;
   k.T = lat->T;

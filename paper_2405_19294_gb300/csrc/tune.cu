@@ -18,20 +18,26 @@
 
 #include "hr_internal.h"
 
-int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out) {
+int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopShape *out) {
   int n = 0;
   const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
+  if (site && multi_rhs) {
+    // links staged once per site for all right-hand sides of a block
+    out[n++] = HopShape{0, 0, 0, 16};
+    out[n++] = HopShape{0, 0, 0, 8};
+    out[n++] = HopShape{0, 0, 0, 32};
+  }
   if (site) {
     // compiler's register choice at 64 / 128 / 32 / 256 threads, then (not
     // for FP64, which is ALU-bound) the high- and low-register budgets
     const int bss[4] = {64, 128, 32, 256};
-    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0};
+    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0, 0};
     if (prec != HR_F64) {
-      out[n++] = HopShape{0, 32, 1};
-      out[n++] = HopShape{0, 64, 1};
-      out[n++] = HopShape{0, 128, 1};
-      out[n++] = HopShape{0, 32, 2};
-      out[n++] = HopShape{0, 64, 2};
+      out[n++] = HopShape{0, 32, 1, 0};
+      out[n++] = HopShape{0, 64, 1, 0};
+      out[n++] = HopShape{0, 128, 1, 0};
+      out[n++] = HopShape{0, 32, 2, 0};
+      out[n++] = HopShape{0, 64, 2, 0};
     }
   }
   if (!clover) {
@@ -46,7 +52,7 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, HopShape *out) {
       if (d == 15 || d == 21) { gs[0] = 4; gs[1] = 8; }
     }
     for (int k = 0; k < 2; ++k)
-      if (gs[k]) out[n++] = HopShape{gs[k], 128, 0};
+      if (gs[k]) out[n++] = HopShape{gs[k], 128, 0, 0};
   }
   return n;
 }
@@ -78,7 +84,7 @@ static bool tuning_enabled() {
 
 int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s) {
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, a.clover != nullptr, shapes);
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, a.clover != nullptr, a.nrhs > 1, shapes);
   if (n == 0) return HR_ERR_UNSUPPORTED;
   const long long key = tune_key(lat, prec, a);
   {
@@ -119,7 +125,7 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 }
 
 // Report the tuned shape for the lattice's hop at (prec, nrhs, clover): returns
-// regs * 10000 + split_g * 1000 + block size, or -1 if that key is not tuned yet.
+// mrhs * 100000 + regs * 10000 + split_g * 1000 + block size, or -1 if not tuned yet.
 extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover) {
   if (!lat) return -1;
   HopArgs a;
@@ -129,15 +135,16 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_best.find(tune_key(lat, prec, a));
   if (it == g_best.end()) return -1;
-  return it->second.regs * 10000 + it->second.split_g * 1000 + it->second.bs;
+  return it->second.mrhs * 100000 + it->second.regs * 10000 + it->second.split_g * 1000 + it->second.bs;
 }
 
-// Candidate shapes of this lattice's hop, encoded regs * 10000 + split_g * 1000 + block size.
-extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clover, int *out, int max) {
-  if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16) return HR_ERR_ARG;
+// Candidate shapes of this lattice's hop, encoded as hr_tuned_shape reports them.
+extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs, int clover, int *out, int max) {
+  if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
-  for (int k = 0; k < n && k < max; ++k) out[k] = shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs;
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
+  for (int k = 0; k < n && k < max; ++k)
+    out[k] = shapes[k].mrhs * 100000 + shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs;
   return n;
 }
 
@@ -146,9 +153,9 @@ extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int clov
 extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape) {
   if (!lat || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, shapes);
+  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n; ++k)
-    if (shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
+    if (shapes[k].mrhs * 100000 + shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
       HopArgs a;
       memset(&a, 0, sizeof(a));
       a.nrhs = nrhs;

@@ -63,7 +63,7 @@ _SIGS = {
                               C.POINTER(hr_cg_stats)]),
     "hr_norm2_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "hr_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
-    "hr_hop_shape_candidates": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "hr_hop_shape_candidates": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "hr_set_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
     "hr_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
     "hr_batch_destroy": (C.c_int, [_P]),
@@ -101,6 +101,14 @@ def _ptr(t) -> int:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("expected a CUDA torch tensor")
     return t.data_ptr()
+
+
+def _ptr_or_pinned(t) -> int:
+    """Device tensor, or page-locked host tensor (read/written by the kernel in place)."""
+    import torch
+    if isinstance(t, torch.Tensor) and (t.is_cuda or t.is_pinned()):
+        return t.data_ptr()
+    raise TypeError("expected a CUDA tensor or a pinned host tensor")
 
 
 class Lattice:
@@ -150,11 +158,11 @@ class Lattice:
         return torch.zeros(self.field_bytes(parity, prec, nrhs), dtype=torch.uint8, device="cuda")
 
     def pack(self, internal, canonical, parity: int, prec: int, nrhs: int = 1):
-        _check(_lib.hr_pack_spinor(self._h, _ptr(internal), _ptr(canonical), parity, prec, nrhs),
+        _check(_lib.hr_pack_spinor(self._h, _ptr(internal), _ptr_or_pinned(canonical), parity, prec, nrhs),
                "hr_pack_spinor")
 
     def unpack(self, canonical, internal, parity: int, prec: int, nrhs: int = 1):
-        _check(_lib.hr_unpack_spinor(self._h, _ptr(canonical), _ptr(internal), parity, prec, nrhs),
+        _check(_lib.hr_unpack_spinor(self._h, _ptr_or_pinned(canonical), _ptr(internal), parity, prec, nrhs),
                "hr_unpack_spinor")
 
     # -- gauge -----------------------------------------------------------
@@ -177,20 +185,27 @@ class Lattice:
         _check(_lib.hr_dphi(self._h, _ptr(out), _ptr(inp), parity, m0, csw, prec, nrhs, int(dagger)),
                "hr_dphi")
 
-    def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
-        """(G threads per site or 0, threads per block, register budget) chosen by the autotuner, or None."""
-        v = _lib.hr_tuned_shape(self._h, prec, nrhs, int(clover))
-        return None if v < 0 else ((v % 10000) // 1000, v % 1000, v // 10000)
+    @staticmethod
+    def _decode(v):
+        return ((v % 10000) // 1000, v % 1000, (v % 100000) // 10000, v // 100000)
 
-    def shape_candidates(self, prec: int, clover: bool = False):
+    def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
+        """(G threads per site or 0, threads per block, register budget, multi-rhs sites per block)
+        chosen by the autotuner, or None."""
+        v = _lib.hr_tuned_shape(self._h, prec, nrhs, int(clover))
+        return None if v < 0 else self._decode(v)
+
+    def shape_candidates(self, prec: int, nrhs: int = 1, clover: bool = False):
         buf = (C.c_int * 16)()
-        n = _lib.hr_hop_shape_candidates(self._h, prec, int(clover), buf, 16)
+        n = _lib.hr_hop_shape_candidates(self._h, prec, nrhs, int(clover), buf, 16)
         if n < 0:
             raise HrError(n, "hr_hop_shape_candidates")
-        return [((v % 10000) // 1000, v % 1000, v // 10000) for v in buf[:min(n, 16)]]
+        return [self._decode(v) for v in buf[:min(n, 16)]]
 
     def set_shape(self, prec: int, shape, nrhs: int = 1, clover: bool = False):
-        code = shape[2] * 10000 + shape[0] * 1000 + shape[1]
+        g, bs, regs = shape[0], shape[1], shape[2]
+        mr = shape[3] if len(shape) > 3 else 0
+        code = mr * 100000 + regs * 10000 + g * 1000 + bs
         _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), code), "hr_set_tuned_shape")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):

@@ -239,3 +239,50 @@ def test_autotuner_records_a_choice(hr):
     _gpu_apply(lat, psi, 0, -0.4, 0.0, 1, 0)
     sh = lat.tuned_shape(1)
     assert sh is not None and sh in lat.shape_candidates(1)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_pack_unpack_direct_from_pinned_host(hr, prec):
+    """Page-locked host buffers are read / written by the kernels in place (no staging copy)."""
+    import ctypes
+    T, L, N, rep = 6, 4, 3, "fund"
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
+    psi = inputs.gaussian_spinor(9, T, L, lat.d, nrhs=2)
+    host = torch.from_numpy(np.stack([psi.real, psi.imag], -1)).pin_memory()
+    dev = host.cuda()
+    f_host, f_dev = lat.new_field(0, prec, 2), lat.new_field(0, prec, 2)
+    lat.pack(f_host, host, 0, prec, 2)
+    lat.pack(f_dev, dev, 0, prec, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(f_host, f_dev)
+    out_host = torch.zeros_like(host).pin_memory()
+    out_dev = torch.zeros_like(dev)
+    lat.unpack(out_host, f_dev, 0, prec, 2)
+    lat.unpack(out_dev, f_dev, 0, prec, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(out_host, out_dev.cpu())
+    # pageable host memory is refused by the C ABI (nothing is launched)
+    page = np.zeros(host.numel(), dtype=np.float64)
+    lib = hr.lib_handle()
+    rc = lib.hr_pack_spinor(lat._h, ctypes.c_void_p(f_dev.data_ptr()), ctypes.c_void_p(page.ctypes.data), 0, prec, 2)
+    assert rc == -1
+
+
+@pytest.mark.parametrize("N,rep,csw", [(3, "fund", 0.0), (3, "sym", 1.0), (2, "adj", 0.0), (3, "adj", 1.0),
+                                       (6, "adj", 0.0)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_every_multi_rhs_shape_is_correct(hr, N, rep, csw, prec):
+    """Several right-hand sides at once, every candidate shape (incl. the link-staging kernel)."""
+    T, L, m0, eps, nrhs = 4, 6, -0.35, 1.0, 5
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, csw)
+    op = oracle_operator(T, L, N, rep, eps, m0, csw)
+    psi = inputs.gaussian_spinor(12, T, L, lat.d, nrhs)
+    mask = op.geom.parity == 0
+    refs = [_oracle_apply(op, psi[r], 0, 0) for r in range(nrhs)]
+    shapes = lat.shape_candidates(prec, nrhs=nrhs, clover=csw != 0.0)
+    assert len(shapes) >= 1
+    for sh in shapes:
+        lat.set_shape(prec, sh, nrhs=nrhs, clover=csw != 0.0)
+        got = _gpu_apply(lat, psi, 0, m0, csw, prec, 0, nrhs=nrhs)
+        for r in range(nrhs):
+            assert rel_err(got[r], refs[r], mask) < TOL[prec], (sh, r)
