@@ -288,11 +288,36 @@ def run_suite(args):
         lat.close()
         del fb, fx
         torch.cuda.empty_cache()
+    if "bicg" in which:
+        out.append(_suite_bicgstab(hr, inputs, torch))
     if "c3" in which:
         out.append(_suite_c3(hr, inputs, torch))
     if "c4" in which:
         out.append(_suite_c4(hr, inputs, torch))
     return out
+
+
+def _suite_bicgstab(hr, inputs, torch):
+    """BiCGstab on Dhat directly vs CG on the normal equations, SU(3) fund 32^3 x 64, to 1e-10."""
+    T, L, N, rep, m0 = 64, 32, 3, "fund", -0.4
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+    fb = _pack_rhs(lat, inputs, torch, 1, T, L, 1, hr.F64)
+    fx = lat.new_field(0, hr.F64)
+    line = {"suite": "SU(3) fund 32^3x64: BiCGstab on Dhat vs CG on Dhat^+Dhat, to 1e-10", "m0": m0,
+            "note": "BiCGstab residual is |b - Dhat x|/|b|; CG residual is that of the normal system"}
+    for name, fn, inner in (("cg_fp64", lat.cg_solve, hr.F64), ("cg_mixed_fp32", lat.cg_solve, hr.F32),
+                            ("bicgstab_fp64", lat.bicgstab_solve, hr.F64),
+                            ("bicgstab_mixed_fp32", lat.bicgstab_solve, hr.F32)):
+        r = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=inner, check_every=10, raise_on_error=False)
+            r["wall_s"] = round(time.perf_counter() - t0, 4)
+        line[name] = {k: r[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
+    print(json.dumps(line), flush=True)
+    lat.close()
+    return line
 
 
 def _suite_c3(hr, inputs, torch):
@@ -388,8 +413,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default="", help="comma list of c2,c3,c4: measure those workloads instead")
-    ap.add_argument("--shape", default="", help="pin the FP32 hop shape 'regs,G,block' (profiling runs only)")
+    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4: measure those workloads instead")
+    ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
+    ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
     ap.add_argument("--L", type=int, default=WORKLOAD["L"], help="space extent (profiling runs only)")
     args = ap.parse_args()
@@ -427,12 +453,13 @@ def main():
     del psi
     src = src_host.cuda()
     stream = torch.cuda.current_stream()
+    TP = hr.F32 if args.prec == "f32" else hr.F16   # timed precision
     if args.shape:
         regs, g, bs = (int(v) for v in args.shape.split(","))
-        lat.set_shape(hr.F32, (g, bs, regs))
-    fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
-    fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32)}
-    for p in (hr.F64, hr.F32):
+        lat.set_shape(TP, (g, bs, regs))
+    fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16)}
+    fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16)}
+    for p in (hr.F64, hr.F32, hr.F16):
         lat.pack(fin[p], src, hr.EVEN, p)
     flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")   # 512 MiB, read to evict L2
     m0, csw = wl["m0"], wl["csw"]
@@ -451,13 +478,13 @@ def main():
 
     clocks = ClockSampler(local)   # runs through warm-up, timed region and the FP64 leg
     for _ in range(args.warmup):
-        lat.dphi(fout[hr.F32], fin[hr.F32], hr.EVEN, m0, csw, hr.F32)
+        lat.dphi(fout[TP], fin[TP], hr.EVEN, m0, csw, TP)
     lat.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    ms32 = timed(hr.F32, args.steps)
+    ms32 = timed(TP, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -465,7 +492,7 @@ def main():
     lat.synchronize()
     ms_step = job_timing(float(np.mean(ms32)), world, dist, device="cuda")
     sites = lat.Vh
-    b32 = bytes_per_even_site(N, rep, 4) * sites
+    b32 = bytes_per_even_site(N, rep, 4 if TP == hr.F32 else 2) * sites
     gbs = job_value(b32, world, ms_step)
 
     # FP64 Dhat (FP64-ALU bound on this part)
@@ -525,14 +552,15 @@ def main():
                 cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[k]["seconds"], 2)
 
     peaks, kind = measured_peaks()
-    traffic = ncu_traffic("dram_bytes_per_even_site_f32")
+    traffic = ncu_traffic(f"dram_bytes_per_even_site_{args.prec}")
     roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(gbs / world / peaks["hbm_gbs"], 4), "peak_kind": kind,
             "traffic": (round(traffic * sites / 2) if traffic else None),
-            "kernel": f"hop_kernel<3,false,1>, tuned shape (G, block) = {lat.tuned_shape(hr.F32)}, 2 launches per Dhat"}
+            "kernel": f"hop_kernel<3,false,{TP}>, tuned shape (G, block, regs, mrhs) = {lat.tuned_shape(TP)}, "
+                      "2 launches per Dhat"}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "SU(3) fund 32^3x64 Dhat even (even-odd Schur), eps=1.0 reunitarised, "
                                    "m0=-0.4", "T": T, "L": L, "N": N, "rep": rep,
                        "l2": "flushed between steps (512 MiB read)", "parallelism": f"replicas x{world}"},

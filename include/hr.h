@@ -153,6 +153,17 @@ int hr_export_represented_links(hr_lattice *lat, double *UR_dev);
  * A(x)^{-1} instead.  Needs csw != 0 at hr_represent_links. */
 int hr_export_clover(hr_lattice *lat, double *A_dev, double m0, int inverse);
 
+/* Choose the form of the clover diagonal (Sec. 3.1, which lists both the
+ * Sheikholeslami-Wohlert term and its exponentiated form of Francis,
+ * Fritzsch, Luscher and Rago).  With C(x) = c_sw (i/4) sigma.Fhat(x):
+ *   on = 0 (default): A(x) = (4 + m0) + C(x)
+ *   on = 1          : A(x) = (4 + m0) exp(C(x) / (4 + m0))
+ * The exponential is taken in FP64 per chiral block (scaling and squaring of
+ * a Taylor series); A^{-1} follows by Gauss-Jordan as for the plain term.
+ * Affects every later hr_dphi / solver / export call on this lattice.
+ * Errors: HR_ERR_ARG (on not 0 or 1; at use, 4 + m0 == 0 with on = 1). */
+int hr_set_clover_exponential(hr_lattice *lat, int on);
+
 /* ---- spinor fields ------------------------------------------------------ */
 
 /* Canonical FP64 spinors psi[nrhs][V][4][d] -> internal field of the given
@@ -254,7 +265,7 @@ int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int
                       const hr_cg_params *params, hr_cg_stats *stats);
 
 /* The hopping-kernel launch shape the autotuner chose for this lattice at
- * (prec, nrhs, clover): mrhs * 100000 + regs * 10000 + split_g * 1000 +
+ * (prec, nrhs, clover): mrhs * 10000000 + regs * 1000000 + split_g * 1000 +
  * threads per block.  mrhs = S > 0: the multi-right-hand-side kernel with S
  * sites per block (links staged once per site for all right-hand sides);
  * split_g = 0: one site per thread with register budget regs = 0 compiler's
@@ -272,6 +283,18 @@ int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs, int clove
  * (reproducible runs, tests of every shape).  HR_ERR_ARG unless `shape` is
  * one of the candidates. */
 int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape);
+
+/* Solve Dhat_p x = b (parity EVEN/ODD) or D x = b (FULL) directly with
+ * BiCGstab (Sec. 3.3; van der Vorst's stabilised bi-conjugate gradient), for
+ * nrhs FP64 internal fields, to a true FP64 relative residual
+ * |b - A x| / |b| <= params->tol per rhs.  inner_prec HR_F64: plain FP64
+ * BiCGstab; HR_F32: FP32 inner BiCGstab inside FP64 defect correction.
+ * x overwritten (x0 = 0).  Synchronous.  The solver's workspace is shared
+ * by all lattices of the process: do not call it concurrently from several
+ * threads.  Errors: HR_ERR_ARG (HR_F16 inner not offered),
+ * HR_ERR_NOT_CONVERGED, HR_ERR_BREAKDOWN (rho or <t,t> vanished). */
+int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
+                      const hr_cg_params *params, hr_cg_stats *stats);
 
 /* Human-readable text of an hr_status. */
 const char *hr_status_string(int status);

@@ -176,9 +176,13 @@ def field_strength(UR: np.ndarray, geom: Geometry, mu: int, nu: int,
 
 
 def clover_matrix(UR: np.ndarray, geom: Geometry, m0: float, csw: float,
-                  sites: np.ndarray | None = None) -> np.ndarray:
+                  sites: np.ndarray | None = None, exponential: bool = False) -> np.ndarray:
     """A(x) = (4 + m0) + c_sw (i/4) sum_{mu != nu} sigma_mu_nu (x) Fhat_mu_nu(x).
 
+    With ``exponential`` the exponentiated clover term the paper supports
+    (Sec. 3.1, after Francis, Fritzsch, Luscher and Rago): with C(x) the
+    clover term above, A(x) = (4 + m0) exp(C(x) / (4 + m0)), the matrix
+    exponential of the full 4d x 4d matrix (scipy's expm).
     Returned as full [n_sites][4d][4d] matrices, index = spin * d + colour.
     """
     if sites is None:
@@ -195,6 +199,11 @@ def clover_matrix(UR: np.ndarray, geom: Geometry, m0: float, csw: float,
                 F = field_strength(UR, geom, mu, nu, sites)
                 A += csw * 0.25j * np.einsum("st,xab->xsatb", sigma(mu, nu), F).reshape(
                     len(sites), 4 * d, 4 * d)
+    if exponential:
+        import scipy.linalg
+        c = 4.0 + m0
+        C = A - c * np.eye(4 * d)
+        A = np.array([c * scipy.linalg.expm(C[k] / c) for k in range(len(sites))])
     return A
 
 
@@ -239,8 +248,9 @@ class WilsonOperator:
     """
 
     def __init__(self, U, N: int, rep: str, geom: Geometry, m0: float,
-                 csw: float = 0.0, link_fn=None):
+                 csw: float = 0.0, link_fn=None, exponential: bool = False):
         self.N, self.rep, self.geom, self.m0, self.csw = N, rep, geom, m0, csw
+        self.exponential = exponential
         self.d = sun.rep_dim(N, rep)
         self.lazy = link_fn is not None
         if self.lazy:
@@ -249,7 +259,7 @@ class WilsonOperator:
             self._A_cache = {}
         else:
             self.UR = represented_field(U, N, rep, geom)
-            self.A = clover_matrix(self.UR, geom, m0, csw) if csw != 0.0 else None
+            self.A = clover_matrix(self.UR, geom, m0, csw, exponential=exponential) if csw != 0.0 else None
 
     # diagonal part --------------------------------------------------------
     def apply_A(self, psi, sites, dagger=False, inverse=False):
@@ -261,7 +271,8 @@ class WilsonOperator:
         if self.lazy:
             need = [int(x) for x in sites if int(x) not in self._A_cache]
             if need:
-                An = clover_matrix(self.UR, self.geom, self.m0, self.csw, np.array(need))
+                An = clover_matrix(self.UR, self.geom, self.m0, self.csw, np.array(need),
+                                   exponential=self.exponential)
                 for k, x in enumerate(need):
                     self._A_cache[x] = An[k]
             A = np.array([self._A_cache[int(x)] for x in sites])

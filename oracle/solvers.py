@@ -1,4 +1,4 @@
-"""Conjugate gradient for the oracle.
+"""Krylov solvers for the oracle: conjugate gradient and BiCGstab.
 
 The paper (Sec. 3.3) lists the conjugate gradient among the GPU-ported
 inverters without spelling it out.  This is textbook Hestenes-Stiefel CG on a
@@ -9,6 +9,13 @@ restart from it (r = p = b - M x) and continue.
 
 For the Wilson operator it is run on the normal equations M = D^dagger D
 (full lattice) or M = Dhat^dagger Dhat (even-odd Schur complement).
+
+The paper (Sec. 3.3) also ports the stabilised bi-conjugate gradient of van
+der Vorst (1992), which solves the non-Hermitian system Dhat x = b directly.
+``bicgstab`` follows that algorithm's steps (shadow residual r^ = r0, one
+BiCG step with coefficient alpha, then a minimal-residual step omega), with
+the same stopping rule as ``cg`` (recursive residual, then the true residual,
+restart from it if needed).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 """
@@ -88,3 +95,50 @@ def solve_wilson_eo(op, b: np.ndarray, tol: float, maxit: int = 100000):
     u[odd_sites] = b[odd_sites] - (-0.5 * hopping(op.UR, xe, g, 1, odd_sites))
     x[odd_sites] = op.apply_A(u[odd_sites], odd_sites, inverse=True)
     return x, it
+
+
+def bicgstab(apply_A, b: np.ndarray, tol: float, maxit: int = 100000):
+    """Solve A x = b (A need not be Hermitian).  Returns (x, iterations, true relative residual).
+
+    Each iteration: rho = <r^, r>; beta = (rho / rho_old)(alpha / omega);
+    p = r + beta (p - omega v); v = A p; alpha = rho / <r^, v>; s = r - alpha v;
+    t = A s; omega = <t, s> / <t, t>; x += alpha p + omega s; r = s - omega t.
+    """
+    bnorm = np.sqrt(vdot(b, b).real)
+    x = np.zeros_like(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    r = b.copy()
+    it = 0
+    while it < maxit:
+        rhat = r.copy()
+        rho_old = alpha = omega = 1.0 + 0.0j
+        v = np.zeros_like(b)
+        p = np.zeros_like(b)
+        restart = False
+        while it < maxit:
+            rho = vdot(rhat, r)
+            beta = (rho / rho_old) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            v = apply_A(p)
+            alpha = rho / vdot(rhat, v)
+            s = r - alpha * v
+            t = apply_A(s)
+            tt = vdot(t, t).real
+            omega = vdot(t, s) / tt if tt > 0 else 0.0
+            x = x + alpha * p + omega * s
+            r = s - omega * t
+            rho_old = rho
+            it += 1
+            if np.sqrt(vdot(r, r).real) <= tol * bnorm:
+                r_true = b - apply_A(x)
+                rt = np.sqrt(vdot(r_true, r_true).real)
+                if rt <= tol * bnorm:
+                    return x, it, rt / bnorm
+                r = r_true
+                restart = True
+                break
+        if not restart:
+            break
+    r_true = b - apply_A(x)
+    return x, it, np.sqrt(vdot(r_true, r_true).real) / bnorm

@@ -35,21 +35,46 @@ struct BLat {         // per-lattice view for the batched vector kernels
 
 struct BClass {
   int d, is_real;
-  HopShape sh;
+  HopShape sh[3];        // launch shape per precision
   std::vector<int> members;
-  int2 *items;  // device work list (lattice index, tile)
-  int nitems;
+  int2 *items[3];        // device work list (lattice index, tile) per precision
+  int nitems[3];
+  int tuned[3];
+};
+
+struct BPair {          // per-lattice (x, y) of a batched y = a x + b y
+  const char *x;
+  char *y;
+  int64_t Vh;
+  int d, nblk;
 };
 
 enum { B_RR0 = 0, B_RR1, B_PAP, B_ALPHA, B_BETA, B_STOP, B_A, B_B, B_OUT, B_NS };
+// batched axpby operand pairs of the outer loop
+enum { P_B_R = 0, P_AP_R, P_R_RL, P_RL_PL, P_XL_X, P_XL_XL, B_NPAIRS };
 
 int launch_multi(int prec, const BClass &c, const HopK *descs, const int *frozen, cudaStream_t s) {
+  const HopShape sh = c.sh[prec];
   switch (prec) {
-    case HR_F64: return hr_launch_hop_multi_f64(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
-    case HR_F32: return hr_launch_hop_multi_f32(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
-    case HR_F16: return hr_launch_hop_multi_f16(c.d, c.is_real, c.sh, descs, c.items, c.nitems, frozen, s);
+    case HR_F64: return hr_launch_hop_multi_f64(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
+    case HR_F32: return hr_launch_hop_multi_f32(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
+    case HR_F16: return hr_launch_hop_multi_f16(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
   }
   return HR_ERR_ARG;
+}
+
+// y = a x + b y per lattice (a, b, skip indexed by lattice), optional |y|^2 per lattice
+template <int PX, int PY>
+__global__ void baxpby_kernel(const BPair *pr, const int2 *items, const double *a, const double *b, RedArgs red,
+                              int want_norm, const int *skip) {
+  typedef typename PT<PY>::A AY;
+  const int2 it = items[blockIdx.x];
+  const BPair P = pr[it.x];
+  double acc = 0.0;
+  if (!(skip && skip[it.x]))
+    acc = axpby_sites<PX, PY>(P.x, P.y, P.Vh, P.d, (AY)a[it.x], (AY)b[it.x],
+                              (int64_t)it.y * blockDim.x + threadIdx.x, (int64_t)P.nblk * blockDim.x);
+  if (want_norm) reduce_publish(acc, red, RED_PLAIN, it.x, it.y, P.nblk);
 }
 
 template <int P>
@@ -92,8 +117,10 @@ struct hr_batch {
   std::vector<BClass> cls;
   cudaStream_t stream;  // caller's stream
   cudaStream_t s;       // internal stream (capturable)
-  HopK *d_desc;         // [4 stages][n]
+  HopK *d_desc;         // [8 stages][n]: inner Dhat, inner Dhat^+, FP64 Dhat, FP64 Dhat^+
   HopK *h_desc;         // pinned staging
+  BPair *d_pairs;       // [B_NPAIRS][n] operand pairs of the batched axpby
+  BPair *h_pairs;
   BLat *d_blat;
   BLat *h_blat;
   int2 *d_bitems;
@@ -103,23 +130,23 @@ struct hr_batch {
   int *iters, *frozen, *err;
   double *partials;
   unsigned *count;
-  int tuned_prec;       // precision the class shapes were tuned for (-1: none)
 };
 
 static double *BS(hr_batch *b, int k) { return b->scal + (size_t)k * b->n; }
 
-static int build_items(BClass &c, const std::vector<hr_lattice *> &lats) {
-  const int tile = c.sh.split_g ? 128 / c.sh.split_g : c.sh.bs;
+static int build_items(BClass &c, const std::vector<hr_lattice *> &lats, int prec) {
+  const HopShape sh = c.sh[prec];
+  const int tile = sh.split_g ? 128 / sh.split_g : sh.bs;
   std::vector<int2> items;
   for (int li : c.members) {
     const int64_t nt = (lats[li]->Vh + tile - 1) / tile;
     for (int64_t t = 0; t < nt; ++t) items.push_back(make_int2(li, (int)t));
   }
-  cudaFree(c.items);
-  c.items = nullptr;
-  c.nitems = (int)items.size();
-  HR_CUDA(cudaMalloc(&c.items, sizeof(int2) * std::max<size_t>(1, items.size())));
-  HR_CUDA(cudaMemcpy(c.items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  cudaFree(c.items[prec]);
+  c.items[prec] = nullptr;
+  c.nitems[prec] = (int)items.size();
+  HR_CUDA(cudaMalloc(&c.items[prec], sizeof(int2) * std::max<size_t>(1, items.size())));
+  HR_CUDA(cudaMemcpy(c.items[prec], items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   return HR_OK;
 }
 
@@ -135,7 +162,6 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
   b->n = n;
   b->lats.assign(lats, lats + n);
   b->stream = lats[0]->stream;
-  b->tuned_prec = -1;
   std::map<int, int> cidx;
   for (int i = 0; i < n; ++i) {
     const int key = lats[i]->d * 2 + lats[i]->is_real;
@@ -144,14 +170,17 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
       BClass c;
       c.d = lats[i]->d;
       c.is_real = lats[i]->is_real;
-      c.items = nullptr;
-      c.nitems = 0;
-      HopShape shapes[HR_MAX_SHAPES];
-      if (hr_hop_shapes(c.d, c.is_real, HR_F32, 0, 0, shapes) < 1) {
-        delete b;
-        return HR_ERR_UNSUPPORTED;
+      for (int q = 0; q < 3; ++q) {
+        HopShape shapes[HR_MAX_SHAPES];
+        if (hr_hop_shapes(c.d, c.is_real, q, 0, 0, shapes) < 1) {
+          delete b;
+          return HR_ERR_UNSUPPORTED;
+        }
+        c.sh[q] = shapes[0];
+        c.items[q] = nullptr;
+        c.nitems[q] = 0;
+        c.tuned[q] = 0;
       }
-      c.sh = shapes[0];
       cidx[key] = (int)b->cls.size();
       b->cls.push_back(c);
       it = cidx.find(key);
@@ -160,7 +189,8 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
   }
   int rc = HR_OK;
   for (auto &c : b->cls)
-    if (rc == HR_OK) rc = build_items(c, b->lats);
+    for (int q = 0; q < 3; ++q)
+      if (rc == HR_OK) rc = build_items(c, b->lats, q);
   std::vector<int2> bitems;
   for (int i = 0; i < n; ++i) {
     const int nblk = hr_blas_blocks(lats[i]->Vh);
@@ -174,8 +204,10 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
     }
   };
   A(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
-  A(cudaMalloc(&b->d_desc, sizeof(HopK) * 4 * n));
-  A(cudaMallocHost(&b->h_desc, sizeof(HopK) * 4 * n));
+  A(cudaMalloc(&b->d_desc, sizeof(HopK) * 8 * n));
+  A(cudaMallocHost(&b->h_desc, sizeof(HopK) * 8 * n));
+  A(cudaMalloc(&b->d_pairs, sizeof(BPair) * B_NPAIRS * n));
+  A(cudaMallocHost(&b->h_pairs, sizeof(BPair) * B_NPAIRS * n));
   A(cudaMalloc(&b->d_blat, sizeof(BLat) * n));
   A(cudaMallocHost(&b->h_blat, sizeof(BLat) * n));
   A(cudaMalloc(&b->d_bitems, sizeof(int2) * bitems.size()));
@@ -207,9 +239,12 @@ extern "C" int hr_batch_destroy(hr_batch *b) {
     cudaStreamSynchronize(b->s);
     cudaStreamDestroy(b->s);
   }
-  for (auto &c : b->cls) cudaFree(c.items);
+  for (auto &c : b->cls)
+    for (int q = 0; q < 3; ++q) cudaFree(c.items[q]);
   cudaFree(b->d_desc);
   cudaFreeHost(b->h_desc);
+  cudaFree(b->d_pairs);
+  cudaFreeHost(b->h_pairs);
   cudaFree(b->d_blat);
   cudaFreeHost(b->h_blat);
   cudaFree(b->d_bitems);
@@ -266,22 +301,23 @@ static int fill_desc(hr_batch *b, int slot0, int prec, void *const *out, const v
 
 // Pick each class's launch shape by timing its candidates on stage 0 of the
 // uploaded descriptors (persistent multi-lattice launches).
-static int tune_classes(hr_batch *b, int prec, cudaStream_t s) {
-  if (b->tuned_prec == prec) return HR_OK;
+static int tune_classes(hr_batch *b, int prec, int slot0, cudaStream_t s) {
   cudaEvent_t e0, e1;
   HR_CUDA(cudaEventCreate(&e0));
   HR_CUDA(cudaEventCreate(&e1));
   for (auto &c : b->cls) {
+    if (c.tuned[prec]) continue;
     HopShape shapes[HR_MAX_SHAPES];
     const int ns = hr_hop_shapes(c.d, c.is_real, prec, 0, 0, shapes);
     float best = 1e30f;
     HopShape bs = shapes[0];
+    const HopK *descs = b->d_desc + (size_t)slot0 * b->n;
     for (int k = 0; k < ns; ++k) {
-      c.sh = shapes[k];
-      HR_TRY(build_items(c, b->lats));
-      HR_TRY(launch_multi(prec, c, b->d_desc, nullptr, s));
+      c.sh[prec] = shapes[k];
+      HR_TRY(build_items(c, b->lats, prec));
+      HR_TRY(launch_multi(prec, c, descs, nullptr, s));
       HR_CUDA(cudaEventRecord(e0, s));
-      for (int r = 0; r < 3; ++r) HR_TRY(launch_multi(prec, c, b->d_desc, nullptr, s));
+      for (int r = 0; r < 3; ++r) HR_TRY(launch_multi(prec, c, descs, nullptr, s));
       HR_CUDA(cudaEventRecord(e1, s));
       HR_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -291,12 +327,12 @@ static int tune_classes(hr_batch *b, int prec, cudaStream_t s) {
         bs = shapes[k];
       }
     }
-    c.sh = bs;
-    HR_TRY(build_items(c, b->lats));
+    c.sh[prec] = bs;
+    c.tuned[prec] = 1;
+    HR_TRY(build_items(c, b->lats, prec));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->tuned_prec = prec;
   return HR_OK;
 }
 
@@ -317,7 +353,7 @@ extern "C" int hr_batch_dphi(hr_batch *b, void *const *out, const void *const *i
   HR_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(HopK) * 2 * b->n, cudaMemcpyHostToDevice, b->stream));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   HR_CUDA(cudaStreamIsCapturing(b->stream, &cap));
-  if (cap == cudaStreamCaptureStatusNone) HR_TRY(tune_classes(b, prec, b->stream));
+  if (cap == cudaStreamCaptureStatusNone) HR_TRY(tune_classes(b, prec, 0, b->stream));
   HR_TRY(batch_dhat(b, prec, 0, nullptr, b->stream));
   for (auto *lat : b->lats) lat->hop_launches += 2;
   return HR_OK;
@@ -365,7 +401,7 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   HR_TRY(fill_desc(b, 2, lo, Apl.data(), (const void *const *)tl.data(), parity, m0, 1));  // Ap = Dhat^+ t
   HR_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(HopK) * 4 * n, cudaMemcpyHostToDevice, s));
   HR_CUDA(cudaMemcpyAsync(b->d_blat, b->h_blat, sizeof(BLat) * n, cudaMemcpyHostToDevice, s));
-  HR_TRY(tune_classes(b, lo, s));
+  HR_TRY(tune_classes(b, lo, 0, s));
   HR_CUDA(cudaMemsetAsync(b->iters, 0, sizeof(int) * n, s));
 
   RedArgs red;
@@ -419,60 +455,82 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   cudaGraphDestroy(graph);
   HR_CUDA(ce);
 
-  // FP64 outer loop
-  std::vector<double> bn2(n), rn2(n), hv(n);
-  std::vector<int> active(n, 1);
+  // ---------------------------------------------------------- FP64 outer loop
+  // Every outer-loop vector operation is one batched launch over all lattices
+  // (per-lattice a, b and skip flags); the FP64 true residual uses the
+  // multi-lattice FP64 hop (descriptor stages 4..7).
+  std::vector<void *> t64(n), Ap64(n), r64(n);
+  for (int i = 0; i < n; ++i) {
+    t64[i] = hr_cg_field(b->lats[i], HR_F64, 3);
+    Ap64[i] = hr_cg_field(b->lats[i], HR_F64, 2);
+    r64[i] = hr_cg_field(b->lats[i], HR_F64, 0);
+  }
+  HR_TRY(fill_desc(b, 4, HR_F64, t64.data(), (const void *const *)x, parity, m0, 0));        // t = Dhat x
+  HR_TRY(fill_desc(b, 6, HR_F64, Ap64.data(), (const void *const *)t64.data(), parity, m0, 1));  // Ap = Dhat^+ t
+  for (int i = 0; i < n; ++i) {
+    hr_lattice *lat = b->lats[i];
+    const int nblk = hr_blas_blocks(lat->Vh);
+    auto pair = [&](int which, const void *px, void *py) {
+      b->h_pairs[(size_t)which * n + i] = BPair{(const char *)px, (char *)py, lat->Vh, lat->d, nblk};
+    };
+    pair(P_B_R, bsrc[i], r64[i]);
+    pair(P_AP_R, Ap64[i], r64[i]);
+    pair(P_R_RL, r64[i], b->h_blat[i].r);
+    pair(P_RL_PL, b->h_blat[i].r, pl[i]);
+    pair(P_XL_X, b->h_blat[i].x, x[i]);
+    pair(P_XL_XL, b->h_blat[i].x, b->h_blat[i].x);
+  }
+  HR_CUDA(cudaMemcpyAsync(b->d_desc + (size_t)4 * n, b->h_desc + (size_t)4 * n, sizeof(HopK) * 4 * n,
+                          cudaMemcpyHostToDevice, s));
+  HR_CUDA(cudaMemcpyAsync(b->d_pairs, b->h_pairs, sizeof(BPair) * B_NPAIRS * n, cudaMemcpyHostToDevice, s));
+  HR_TRY(tune_classes(b, HR_F64, 4, s));
+  int *skip = b->frozen;  // reused between phases: 1 = lattice done (outer) / frozen (inner)
+  std::vector<double> bn2(n), rn2(n);
+  std::vector<int> active(n, 1), skipv(n);
   auto set = [&](int which, const std::vector<double> &v) -> int {
     HR_CUDA(cudaMemcpyAsync(BS(b, which), v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     HR_CUDA(cudaStreamSynchronize(s));
     return HR_OK;
   };
-  // per-lattice FP64 helpers (slot 0 of each lattice's own reduction scratch)
-  auto lat_red = [&](hr_lattice *lat) {
-    RedArgs r;
-    memset(&r, 0, sizeof(r));
-    r.partials = lat->red_partials;
-    r.count = lat->red_count;
-    r.out = lat->red_out;
-    r.err = lat->dev_err;
-    return r;
-  };
-  auto fd = [&](hr_lattice *lat, int prec) {
-    FieldDesc f;
-    f.Vh = lat->Vh;
-    f.d = lat->d;
-    f.fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
-    f.nsub = 1;
-    return f;
-  };
-  // scalar constants on the device: a, b per lattice in B_A / B_B
-  std::vector<double> va(n), vb(n);
-  auto residual = [&](int i) -> int {  // r = b - M x (FP64) -> rn2[i]
-    hr_lattice *lat = b->lats[i];
-    void *r = hr_cg_field(lat, HR_F64, 0), *Ap = hr_cg_field(lat, HR_F64, 2), *t = hr_cg_field(lat, HR_F64, 3);
-    HR_TRY(hr_dphi_impl(lat, t, x[i], parity, m0[i], 0.0, HR_F64, 1, 0, s));
-    HR_TRY(hr_dphi_impl(lat, Ap, t, parity, m0[i], 0.0, HR_F64, 1, 1, s));
-    const FieldDesc f = fd(lat, HR_F64);
-    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, bsrc[i], r, f, f, 1, BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
+  auto set_skip = [&]() -> int {
+    for (int i = 0; i < n; ++i) skipv[i] = active[i] ? 0 : 1;
+    HR_CUDA(cudaMemcpyAsync(skip, skipv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    HR_CUDA(cudaStreamSynchronize(s));
     return HR_OK;
   };
+  RedArgs rn = red;
+  rn.out = BS(b, B_OUT);
+  rn.frozen = nullptr;
+  const dim3 agrid(b->nbitems);
+  auto axpby = [&](int which, int px, int py, int norm) -> int {
+    const BPair *pp = b->d_pairs + (size_t)which * n;
+#define BAX(X, Y) baxpby_kernel<X, Y><<<agrid, 256, 0, s>>>(pp, b->d_bitems, BS(b, B_A), BS(b, B_B), rn, norm, skip)
+    if (px == 0 && py == 0) BAX(0, 0);
+    else if (px == 0 && py == 1) BAX(0, 1);
+    else if (px == 1 && py == 0) BAX(1, 0);
+    else if (px == 1 && py == 1) BAX(1, 1);
+    else if (px == 1 && py == 2) BAX(1, 2);
+    else return HR_ERR_UNSUPPORTED;
+#undef BAX
+    return hr_check_launch("baxpby_kernel");
+  };
+  auto fetch_norms = [&](std::vector<double> &v) -> int {
+    HR_CUDA(cudaMemcpyAsync(b->host, BS(b, B_OUT), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    HR_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+      if (active[i]) v[i] = b->host[i];
+    return HR_OK;
+  };
+  std::vector<double> one(n, 1.0), zero(n, 0.0), mone(n, -1.0), va(n);
   // x = 0; r = b; |b|^2
-  for (int i = 0; i < n; ++i) {
-    va[i] = 1.0;
-    vb[i] = 0.0;
-  }
-  HR_TRY(set(B_A, va));
-  HR_TRY(set(B_B, vb));
-  for (int i = 0; i < n; ++i) {
-    hr_lattice *lat = b->lats[i];
-    const FieldDesc f = fd(lat, HR_F64);
-    HR_CUDA(cudaMemsetAsync(x[i], 0, f.fb, s));
-    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, bsrc[i], hr_cg_field(lat, HR_F64, 0), f, f, 1, BS(b, B_A) + i,
-                         BS(b, B_B) + i, lat_red(lat), 1, s));
-    HR_CUDA(cudaMemcpyAsync(&b->host[i], lat->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
-  }
-  HR_CUDA(cudaStreamSynchronize(s));
-  for (int i = 0; i < n; ++i) rn2[i] = bn2[i] = b->host[i];
+  for (int i = 0; i < n; ++i)
+    HR_CUDA(cudaMemsetAsync(x[i], 0, hr_spinor_field_bytes(b->lats[i]->Vh, b->lats[i]->d, HR_F64), s));
+  HR_TRY(set_skip());
+  HR_TRY(set(B_A, one));
+  HR_TRY(set(B_B, zero));
+  HR_TRY(axpby(P_B_R, HR_F64, HR_F64, 1));
+  HR_TRY(fetch_norms(bn2));
+  for (int i = 0; i < n; ++i) rn2[i] = bn2[i];
 
   int status = HR_OK, iters = 0, outer = 0;
   const double tol2 = prm->tol * prm->tol;
@@ -488,38 +546,30 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
       break;
     }
     // rl = r / |r|, pl = rl, xl = 0 on active lattices; stop and rr per lattice
-    std::vector<double> stop(n), rr(n), inv(n), one(n, 1.0), zero(n, 0.0);
+    std::vector<double> stop(n), rr(n);
     std::vector<int> frz(n);
     for (int i = 0; i < n; ++i) {
-      const double rn = sqrt(rn2[i]);
-      inv[i] = (active[i] && rn > 0.0) ? 1.0 / rn : 0.0;
-      double tgt = prm->tol * sqrt(bn2[i]) / (2.0 * (rn > 0.0 ? rn : 1.0));
+      const double rnv = sqrt(rn2[i]);
+      va[i] = (active[i] && rnv > 0.0) ? 1.0 / rnv : 0.0;
+      double tgt = prm->tol * sqrt(bn2[i]) / (2.0 * (rnv > 0.0 ? rnv : 1.0));
       if (tgt < inner_tol) tgt = inner_tol;
       stop[i] = active[i] ? tgt * tgt : 1e300;
       rr[i] = active[i] ? 1.0 : 0.0;
       frz[i] = active[i] ? 0 : 1;
     }
-    HR_TRY(set(B_A, inv));
+    HR_TRY(set_skip());
+    HR_TRY(set(B_A, va));
     HR_TRY(set(B_B, zero));
-    for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      hr_lattice *lat = b->lats[i];
-      HR_TRY(hr_blas_axpby(HR_F64, HR_F32, hr_cg_field(lat, HR_F64, 0), b->h_blat[i].r, fd(lat, HR_F64),
-                           fd(lat, HR_F32), 1, BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
-    }
+    HR_TRY(axpby(P_R_RL, HR_F64, HR_F32, 0));
     HR_TRY(set(B_A, one));
-    for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      hr_lattice *lat = b->lats[i];
-      HR_TRY(hr_blas_axpby(HR_F32, lo, b->h_blat[i].r, pl[i], fd(lat, HR_F32), fd(lat, lo), 1, BS(b, B_A) + i,
-                           BS(b, B_B) + i, lat_red(lat), 0, s));
-      HR_CUDA(cudaMemsetAsync(b->h_blat[i].x, 0, fd(lat, HR_F32).fb, s));
-    }
+    HR_TRY(axpby(P_RL_PL, HR_F32, lo, 0));
+    HR_TRY(set(B_A, zero));
+    HR_TRY(axpby(P_XL_XL, HR_F32, HR_F32, 0));  // xl = 0 x + 0 xl
     HR_TRY(set(B_STOP, stop));
     HR_TRY(set(B_RR0, rr));
     HR_CUDA(cudaMemcpyAsync(b->frozen, frz.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     HR_CUDA(cudaStreamSynchronize(s));
-    // inner chunks
+    // inner chunks (the graph's kernels read b->frozen, maintained on the device)
     int done = 0;
     while (iters + done < maxit) {
       HR_CUDA(cudaGraphLaunch(exec, s));
@@ -539,36 +589,21 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
       status = HR_ERR_BREAKDOWN;
       break;
     }
-    // x += |r| xl; r = b - M x
-    std::vector<double> rnv(n);
-    for (int i = 0; i < n; ++i) rnv[i] = sqrt(rn2[i]);
-    HR_TRY(set(B_A, rnv));
+    // x += |r| xl (active lattices), then r = b - M x in FP64
+    HR_TRY(set_skip());
+    for (int i = 0; i < n; ++i) va[i] = sqrt(rn2[i]);
+    HR_TRY(set(B_A, va));
     HR_TRY(set(B_B, one));
-    for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      hr_lattice *lat = b->lats[i];
-      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, b->h_blat[i].x, x[i], fd(lat, HR_F32), fd(lat, HR_F64), 1,
-                           BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 0, s));
-    }
-    // r = 1*b + 0*r, then r = -1*Ap + 1*r with |r|^2
+    HR_TRY(axpby(P_XL_X, HR_F32, HR_F64, 0));
+    HR_TRY(batch_dhat(b, HR_F64, 4, skip, s));
+    HR_TRY(batch_dhat(b, HR_F64, 6, skip, s));
     HR_TRY(set(B_A, one));
     HR_TRY(set(B_B, zero));
-    for (int i = 0; i < n; ++i)
-      if (active[i]) HR_TRY(residual(i));
-    std::vector<double> mone(n, -1.0);
+    HR_TRY(axpby(P_B_R, HR_F64, HR_F64, 0));
     HR_TRY(set(B_A, mone));
     HR_TRY(set(B_B, one));
-    for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      hr_lattice *lat = b->lats[i];
-      const FieldDesc f = fd(lat, HR_F64);
-      HR_TRY(hr_blas_axpby(HR_F64, HR_F64, hr_cg_field(lat, HR_F64, 2), hr_cg_field(lat, HR_F64, 0), f, f, 1,
-                           BS(b, B_A) + i, BS(b, B_B) + i, lat_red(lat), 1, s));
-      HR_CUDA(cudaMemcpyAsync(&b->host[i], lat->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    HR_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < n; ++i)
-      if (active[i]) rn2[i] = b->host[i];
+    HR_TRY(axpby(P_AP_R, HR_F64, HR_F64, 1));
+    HR_TRY(fetch_norms(rn2));
   }
   cudaGraphExecDestroy(exec);
   HR_CUDA(cudaStreamSynchronize(s));

@@ -14,7 +14,13 @@
 // Mixed precision is defect correction: the FP64 residual r = b - M x is
 // rescaled to unit norm, the inner CG (FP32, or FP16 operator fields with
 // per-site scales and FP32 x, r) reduces it by inner_tol, x += |r| e in FP64,
-// and r is recomputed exactly in FP64, until |r| <= tol |b|.
+// and r is recomputed exactly in FP64, until |r| <= tol |b|.  With an FP16
+// inner solver a middle level sits in between: the FP16 CG restarts from FP32
+// true residuals (r32 - M e32, FP32 operator) until the FP32 system has
+// dropped by HR_MID_TOL, and only then is the (expensive on this part) FP64
+// residual recomputed -- as many FP64 residuals as FP32-inner needs.
+#define HR_MID_TOL 1e-5
+#include <algorithm>
 #include <chrono>
 #include <math.h>
 #include <string.h>
@@ -24,7 +30,7 @@
 
 struct hr_cg_work {
   size_t cap[3];        // bytes per buffer set, per precision
-  void *f[3][5];        // per precision: r, p, Ap, t, x(low)
+  void *f[3][6];        // per precision: r, p, Ap, t, x(low), spare
   double *scal;         // device scalars: [NS][HR_MAX_RHS]
   double *host;         // pinned mirror
   int *iters;           // [HR_MAX_RHS]
@@ -37,7 +43,7 @@ void hr_cg_free(hr_lattice *lat) {
   hr_cg_work *w = lat->cg;
   if (!w) return;
   for (int p = 0; p < 3; ++p)
-    for (int q = 0; q < 5; ++q) cudaFree(w->f[p][q]);
+    for (int q = 0; q < 6; ++q) cudaFree(w->f[p][q]);
   cudaFree(w->scal);
   cudaFree(w->iters);
   cudaFreeHost(w->host);
@@ -59,12 +65,12 @@ static int cg_work(hr_lattice *lat, int prec, size_t bytes) {
   }
   hr_cg_work *w = lat->cg;
   if (w->cap[prec] < bytes) {
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
       cudaFree(w->f[prec][q]);
       w->f[prec][q] = nullptr;
     }
     w->cap[prec] = 0;
-    for (int q = 0; q < 5; ++q) HR_CUDA(cudaMalloc(&w->f[prec][q], bytes));
+    for (int q = 0; q < 6; ++q) HR_CUDA(cudaMalloc(&w->f[prec][q], bytes));
     w->cap[prec] = bytes;
   }
   return HR_OK;
@@ -357,11 +363,74 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
       iters += done;
       ++outer;
       if (status != HR_OK) break;
-      // x += |r| xl
+      void *xacc = xl;  // the correction to add to x (FP32, unit-norm system)
+      if (lo == HR_F16) {
+        // middle level: e32 accumulates FP16 solves; rm = r32 - M e32 in FP32
+        void *r32 = w->f[HR_F32][5], *e32 = w->f[HR_F32][1], *Ap32 = w->f[HR_F32][2], *t32 = w->f[HR_F32][3];
+        double m2[HR_MAX_RHS], mx[HR_MAX_RHS], mz[HR_MAX_RHS], mo[HR_MAX_RHS], minv[HR_MAX_RHS];
+        for (int q = 0; q < nrhs; ++q) {
+          mx[q] = 1.0;
+          mz[q] = 0.0;
+          mo[q] = -1.0;
+        }
+        // r32 = rl_initial is gone (rl was iterated); rebuild it from r: r32 = r / |r|
+        HR_TRY(set_scalars(c, S_A, a));  // a = 1/|r| still
+        HR_TRY(set_scalars(c, S_B, mz));
+        HR_TRY(hr_blas_axpby(HR_F64, HR_F32, r, r32, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+        // e32 = xl
+        HR_TRY(set_scalars(c, S_A, mx));
+        HR_TRY(hr_blas_axpby(HR_F32, HR_F32, xl, e32, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+        for (int mid = 0; mid < 20; ++mid) {
+          // rm (in rl) = r32 - M e32, |rm|^2
+          HR_TRY(hr_dphi_impl(lat, t32, e32, parity, m0, csw, HR_F32, nrhs, 0, c.s));
+          HR_TRY(hr_dphi_impl(lat, Ap32, t32, parity, m0, csw, HR_F32, nrhs, 1, c.s));
+          HR_TRY(set_scalars(c, S_A, mx));
+          HR_TRY(set_scalars(c, S_B, mz));
+          HR_TRY(hr_blas_axpby(HR_F32, HR_F32, r32, rl, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+          HR_TRY(set_scalars(c, S_A, mo));
+          HR_TRY(set_scalars(c, S_B, mx));
+          HR_TRY(hr_blas_axpby(HR_F32, HR_F32, Ap32, rl, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
+          HR_CUDA(cudaMemcpyAsync(m2, S(w, S_OUT), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c.s));
+          HR_CUDA(cudaStreamSynchronize(c.s));
+          bool mid_done = true;
+          for (int q = 0; q < nrhs; ++q) {
+            const double goal = std::max(HR_MID_TOL, 0.5 * prm->tol * sqrt(bn2[q] / rn2[q]));
+            if (!(m2[q] <= goal * goal)) mid_done = false;
+          }
+          if (mid_done || iters >= maxit) break;
+          // next FP16 solve on M e' = rm / |rm|, then e32 += |rm| e'
+          for (int q = 0; q < nrhs; ++q) {
+            const double rn = sqrt(m2[q]);
+            minv[q] = rn > 0.0 ? 1.0 / rn : 0.0;
+            double tg = std::max(inner_tol, 0.5 * prm->tol * sqrt(bn2[q] / rn2[q]) / (rn > 0.0 ? rn : 1.0));
+            stop[q] = rn > 0.0 ? tg * tg : 1e300;
+            rr[q] = rn > 0.0 ? 1.0 : 0.0;
+          }
+          HR_TRY(set_scalars(c, S_A, minv));
+          HR_TRY(set_scalars(c, S_B, mz));
+          HR_TRY(hr_blas_axpby(HR_F32, HR_F32, rl, rl, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+          HR_TRY(set_scalars(c, S_A, mx));
+          HR_TRY(hr_blas_axpby(HR_F32, lo, rl, pl, f32, flo, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+          HR_CUDA(cudaMemsetAsync(xl, 0, fb32 * nsub * nrhs, c.s));
+          HR_TRY(set_scalars(c, S_STOP, stop));
+          HR_TRY(set_scalars(c, S_RR0, rr));
+          done = 0;
+          status = cg_loop(c, HR_F32, lo, xl, rl, pl, Apl, tl, f32, flo, check_every, maxit - iters, &done);
+          iters += done;
+          if (status != HR_OK) break;
+          for (int q = 0; q < nrhs; ++q) minv[q] = sqrt(m2[q]);
+          HR_TRY(set_scalars(c, S_A, minv));
+          HR_TRY(set_scalars(c, S_B, mx));
+          HR_TRY(hr_blas_axpby(HR_F32, HR_F32, xl, e32, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+        }
+        if (status != HR_OK) break;
+        xacc = e32;
+      }
+      // x += |r| xacc
       for (int q = 0; q < nrhs; ++q) a[q] = sqrt(rn2[q]);
       HR_TRY(set_scalars(c, S_A, a));
       HR_TRY(set_scalars(c, S_B, one));
-      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, xl, x, f32, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, xacc, x, f32, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
       HR_TRY(true_residual(c, r, b, x, Ap, t, f64, rn2));
     }
   }

@@ -203,10 +203,41 @@ int hr_clover_build(hr_lattice *lat) {
   return HR_OK;
 }
 
-// A = (4 + m0) + C and A^{-1}, per chiral block, by Gauss-Jordan elimination
-// with partial pivoting in FP64.
+// exp(X) of an n x n complex matrix in place, by scaling and squaring: with
+// 2^s >= 4 |X|_F, Y = X / 2^s has norm <= 1/4, its Taylor series is summed to
+// order 16 by Horner's rule (truncation below 1e-23 relative), and the result
+// is squared s times.  E and W are n x n scratch.
+__device__ void expm_taylor(zd *X, zd *E, zd *W, int n) {
+  double f = 0.0;
+  for (int e = 0; e < n * n; ++e) f += X[e].x * X[e].x + X[e].y * X[e].y;
+  f = sqrt(f);
+  int s = 0;
+  while (f > 0.25 && s < 60) {
+    f *= 0.5;
+    ++s;
+  }
+  const double sc = ldexp(1.0, -s);
+  for (int e = 0; e < n * n; ++e) X[e] = mk(X[e].x * sc, X[e].y * sc);
+  for (int e = 0; e < n * n; ++e) E[e] = mk((e / n == e % n) ? 1.0 : 0.0, 0.0);
+  for (int q = 16; q >= 1; --q) {  // E <- 1 + Y E / q
+    matmul(X, E, W, n, false, false);
+    const double iq = 1.0 / q;
+    for (int e = 0; e < n * n; ++e) E[e] = mk(W[e].x * iq + ((e / n == e % n) ? 1.0 : 0.0), W[e].y * iq);
+  }
+  for (int r = 0; r < s; ++r) {
+    matmul(E, E, W, n, false, false);
+    for (int e = 0; e < n * n; ++e) E[e] = W[e];
+  }
+  for (int e = 0; e < n * n; ++e) X[e] = E[e];
+}
+
+// A = (4 + m0) + C, or with `expo` the exponentiated clover term of Francis,
+// Fritzsch, Luscher and Rago (Sec. 3.1): A = (4 + m0) exp(C / (4 + m0));
+// and A^{-1}, per chiral block, by Gauss-Jordan elimination with partial
+// pivoting in FP64.  exp maps each chiral block to itself, so the exponential
+// is taken block by block.
 __global__ void clover_diag_kernel(void *A64, void *A32, void *I64, void *I32, const void *term, ClK k,
-                                   double m0) {
+                                   double m0, int expo) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (parity, block, site)
   if (g >= 4 * k.Vh) return;
   const int64_t i = g % k.Vh;
@@ -225,6 +256,13 @@ __global__ void clover_diag_kernel(void *A64, void *A32, void *I64, void *I32, c
         M[c * n + r] = mk(v.x, -v.y);
       }
     }
+  if (expo) {  // M <- c exp((M - c) / c), Inv as scratch
+    zd W[4 * HR_CLOVER_MAX_D * HR_CLOVER_MAX_D];
+    const double c = 4.0 + m0, ic = 1.0 / c;
+    for (int e = 0; e < n * n; ++e) M[e] = mk((M[e].x - ((e / n == e % n) ? c : 0.0)) * ic, M[e].y * ic);
+    expm_taylor(M, Inv, W, n);
+    for (int e = 0; e < n * n; ++e) M[e] = mk(M[e].x * c, M[e].y * c);
+  }
   // store A
   double2 *a64 = reinterpret_cast<double2 *>(A64);
   float2 *a32 = reinterpret_cast<float2 *>(A32);
@@ -296,6 +334,7 @@ __global__ void clover_diag_kernel(void *A64, void *A32, void *I64, void *I32, c
 int hr_clover_prepare(hr_lattice *lat, double m0) {
   if (!lat->clover_term) return HR_ERR_STATE;
   if (lat->clover_cached && lat->clover_m0 == m0) return HR_OK;
+  if (lat->clover_exp && 4.0 + m0 == 0.0) return HR_ERR_ARG;
   const int d = lat->d;
   const size_t n64 = (size_t)2 * 4 * d * d * (size_t)lat->Vh * 16u;
   for (int q = 0; q < 2; ++q) {
@@ -312,10 +351,17 @@ int hr_clover_prepare(hr_lattice *lat, double m0) {
   k.T = lat->T;
   const int64_t nt = 4 * lat->Vh;
   clover_diag_kernel<<<(unsigned)((nt + 63) / 64), 64, 0, lat->stream>>>(
-      lat->clover_A[0], lat->clover_A[1], lat->clover_Ainv[0], lat->clover_Ainv[1], lat->clover_term, k, m0);
+      lat->clover_A[0], lat->clover_A[1], lat->clover_Ainv[0], lat->clover_Ainv[1], lat->clover_term, k, m0, lat->clover_exp);
   HR_TRY(hr_check_launch("clover_diag_kernel"));
   lat->clover_m0 = m0;
   lat->clover_cached = 1;
+  return HR_OK;
+}
+
+extern "C" int hr_set_clover_exponential(hr_lattice *lat, int on) {
+  if (!lat || (on != 0 && on != 1)) return HR_ERR_ARG;
+  if (lat->clover_exp != on) lat->clover_cached = 0;
+  lat->clover_exp = on;
   return HR_OK;
 }
 

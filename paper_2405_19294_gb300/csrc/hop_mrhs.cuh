@@ -1,32 +1,50 @@
-// Multi-right-hand-side hopping kernel: one read of each link per site for
-// all right-hand sides of a block.
+// Multi-right-hand-side hopping kernel: one read of each link (and clover
+// block) per site for all right-hand sides of a block.
 //
 // A block covers S consecutive output sites x R right-hand sides (thread t:
 // site t % S, rhs t / S, so each warp reads runs of consecutive sites of one
-// rhs -- coalesced).  For each direction mu the forward links U_R,mu(x) and the
-// backward links U_R,mu(x - mu) of the block's S sites are staged once in
-// shared memory (entry-major, conflict-free) and then used by all R
-// right-hand-side threads of that site; the neighbour spinors are per rhs.
-// Link traffic from L2 / HBM therefore drops by R compared with running the
-// right-hand sides as separate blocks.  The arithmetic per (site, rhs) is the
+// rhs -- coalesced).  The links are staged in shared memory as raw storage
+// chunks ([chunk][site], conflict-free) by asynchronous copies (cp.async),
+// double-buffered by direction: while the block computes direction mu from
+// one buffer, the forward and backward links of direction mu+1 (and, during
+// the last direction, the clover blocks of the epilogue) stream into the other.
+// Link and clover traffic from L2 / HBM therefore drops by R compared with
+// running the right-hand sides as separate blocks, and the staging latency
+// hides behind the arithmetic.  The arithmetic per (site, rhs) is the
 // one-site-per-thread stencil of hop.cuh (same projection table, epilogue).
 #pragma once
 
 #include "hop.cuh"
 
-template <bool REAL, typename A>
-struct LinkEl {
-  typedef cx<A> T;
-};
-template <typename A>
-struct LinkEl<true, A> {
-  typedef A T;
-};
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// chunk k of site s from a staged [chunk][S] array of storage type, converted
+template <int P, int S>
+__device__ __forceinline__ cx<typename PT<P>::A> sm2(const char *base, int k, int s) {
+  if constexpr (P == 0) {
+    const double2 v = reinterpret_cast<const double2 *>(base)[k * S + s];
+    return mk(v.x, v.y);
+  } else if constexpr (P == 1) {
+    const float2 v = reinterpret_cast<const float2 *>(base)[k * S + s];
+    return mk(v.x, v.y);
+  } else {
+    const float2 v = __half22float2(reinterpret_cast<const __half2 *>(base)[k * S + s]);
+    return mk(v.x, v.y);
+  }
+}
 
 template <int D, bool REAL, int P, int MU, bool ADJ, int S>
-__device__ __forceinline__ void hop_dir_smem(cx<typename PT<P>::A> acc[D][4], const void *in, int64_t Vh, int64_t j,
-                                             const typename LinkEl<REAL, typename PT<P>::A>::T (*U)[S], int s,
-                                             typename PT<P>::A sig, typename PT<P>::A scl) {
+__device__ __forceinline__ void hop_dir_staged(cx<typename PT<P>::A> acc[D][4], const void *in, int64_t Vh, int64_t j,
+                                               const char *U, int s, typename PT<P>::A sig,
+                                               typename PT<P>::A scl) {
   typedef typename PT<P>::A A;
   cx<A> h0[D], h1[D];
 #pragma unroll
@@ -45,12 +63,13 @@ __device__ __forceinline__ void hop_dir_smem(cx<typename PT<P>::A> acc[D][4], co
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const int e = ADJ ? (c * D + a) : (a * D + c);
-      if constexpr (REAL) {
-        const A ue = U[e][s];
+      if (REAL) {
+        const cx<A> pr = sm2<P, S>(U, e >> 1, s);
+        const A ue = (e & 1) ? pr.y : pr.x;
         r0 = rfma(ue, h0[c], r0);
         r1 = rfma(ue, h1[c], r1);
       } else {
-        const cx<A> ue = U[e][s];
+        const cx<A> ue = sm2<P, S>(U, e, s);
         if (ADJ) {
           r0 = cfmac(ue, h0[c], r0);
           r1 = cfmac(ue, h1[c], r1);
@@ -64,12 +83,51 @@ __device__ __forceinline__ void hop_dir_smem(cx<typename PT<P>::A> acc[D][4], co
   }
 }
 
-template <int D, bool REAL, int P, int S>
+// B acc for the packed Hermitian chiral blocks staged as [chunk][S] (FP64
+// chunks for FP64 fields, FP32 otherwise)
+template <int D, int P, int S>
+__device__ __forceinline__ void clover_apply_staged(const char *cl, int s, cx<typename PT<P>::A> acc[D][4]) {
+  typedef typename PT<P>::A A;
+  constexpr int PC = (P == 0) ? 0 : 1;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int off = b * 2 * D * D;
+    cx<A> v[2 * D], w[2 * D];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[sp * D + c] = acc[c][2 * b + sp];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const cx<A> dg = sm2<PC, S>(cl, off + q, s);
+      w[2 * q] = scale(dg.x, v[2 * q]);
+      w[2 * q + 1] = scale(dg.y, v[2 * q + 1]);
+    }
+#pragma unroll
+    for (int r = 1; r < 2 * D; ++r)
+#pragma unroll
+      for (int c = 0; c < r; ++c) {
+        const cx<A> a = sm2<PC, S>(cl, off + D + r * (r - 1) / 2 + c, s);
+        w[r] = cfma(a, v[c], w[r]);
+        w[c] = cfmac(a, v[r], w[c]);
+      }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c][2 * b + sp] = w[sp * D + c];
+  }
+}
+
+template <int D, bool REAL, int P, int S, bool CLOVER>
 __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
   typedef typename PT<P>::A A;
-  typedef typename LinkEl<REAL, A>::T LE;
-  __shared__ LE su[2][D * D][S];  // forward / backward links of one direction
-  __shared__ int64_t nbi[8][S];    // neighbour indices of the block's sites
+  constexpr int NCH = REAL ? (D * D + 1) / 2 : D * D;  // link chunks
+  constexpr int ES = (P == 0) ? 16 : (P == 1 ? 8 : 4);  // bytes per link chunk
+  constexpr int CES = (P == 0) ? 16 : 8;                // bytes per clover chunk
+  constexpr int CCH = CLOVER ? 4 * D * D : 1;           // clover chunks per site (both blocks)
+  __shared__ __align__(16) char lbuf[2][2][NCH * S * ES];  // [buffer][forward/backward]
+  __shared__ __align__(16) char cbuf[CCH * S * CES];
+  __shared__ int64_t nbi[8][S];
   const int s = threadIdx.x % S, q = threadIdx.x / S;
   const int nrb = (k.nrhs + R - 1) / R;
   const int64_t tile = blockIdx.x / nrb;
@@ -96,12 +154,33 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
     nbi[6][s] = ii + (int64_t)(zf - st.z) * LLh;
     nbi[7][s] = ii + (int64_t)(zb - st.z) * LLh;
   }
+  __syncthreads();
+  const int64_t slab = (int64_t)k.nch * Vh;
+  // issue the asynchronous copies of direction mu's forward and backward links
+  auto stage_links = [&](int mu, int buf) {
+    const char *lf = reinterpret_cast<const char *>(k.links) + (size_t)((p * 4 + mu) * slab) * ES;
+    const char *lb = reinterpret_cast<const char *>(k.links) + (size_t)(((1 - p) * 4 + mu) * slab) * ES;
+    for (int e = threadIdx.x; e < 2 * NCH * S; e += blockDim.x) {
+      const int side = e / (NCH * S), rem = e % (NCH * S), ch = rem / S, ss = rem % S;
+      if (i0 + ss < Vh) {
+        const int64_t li = side == 0 ? i0 + ss : nbi[2 * mu + 1][ss];
+        const char *src = (side == 0 ? lf : lb) + ((size_t)ch * Vh + li) * ES;
+        cp_async(&lbuf[buf][side][(ch * S + ss) * ES], src, ES);
+      }
+    }
+  };
+  auto stage_clover = [&]() {
+    if (!CLOVER) return;
+    const char *cl = reinterpret_cast<const char *>(k.clover);
+    for (int e = threadIdx.x; e < CCH * S; e += blockDim.x) {
+      const int ch = e / S, ss = e % S;
+      if (i0 + ss < Vh) cp_async(&cbuf[(ch * S + ss) * CES], cl + ((size_t)ch * Vh + i0 + ss) * CES, CES);
+    }
+  };
   const size_t roff = (size_t)(rhs < k.nrhs ? rhs : 0) * k.stride;
   const void *in = reinterpret_cast<const char *>(k.in) + roff;
   void *out = reinterpret_cast<char *>(k.out) + roff;
   const A sg = (A)k.sgn;
-  const int64_t slab = (int64_t)k.nch * Vh;
-  const size_t es = (P == 0) ? 16 : (P == 1 ? 8 : 4);
   const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
   cx<A> acc[D][4];
 #pragma unroll
@@ -109,57 +188,51 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) acc[c][r] = mk(A(0), A(0));
 
+  stage_links(0, 0);
+  cp_async_commit();
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    __syncthreads();  // neighbour indices ready / previous direction's links consumed
-    const char *lf = reinterpret_cast<const char *>(k.links) + (size_t)((p * 4 + mu) * slab) * es;
-    const char *lb = reinterpret_cast<const char *>(k.links) + (size_t)(((1 - p) * 4 + mu) * slab) * es;
-    for (int e = threadIdx.x; e < 2 * D * D * S; e += blockDim.x) {
-      const int side = e / (D * D * S), rem = e % (D * D * S), ent = rem / S, ss = rem % S;
-      if (i0 + ss < Vh) {
-        const int64_t li = side == 0 ? i0 + ss : nbi[2 * mu + 1][ss];
-        const char *lk = side == 0 ? lf : lb;
-        if constexpr (REAL) {
-          const cx<A> pr = ld2<P>(lk, (int64_t)(ent >> 1) * Vh + li);
-          su[side][ent][ss] = (ent & 1) ? pr.y : pr.x;
-        } else {
-          su[side][ent][ss] = ld2<P>(lk, (int64_t)ent * Vh + li);
-        }
-      }
-    }
+    if (mu < 3) stage_links(mu + 1, (mu + 1) & 1);
+    else stage_clover();
+    cp_async_commit();
+    cp_async_wait<1>();  // all but the group just issued: direction mu is in
     __syncthreads();
     if (active) {
       const int64_t jf = nbi[2 * mu][s], jb = nbi[2 * mu + 1][s];
       const A sf = (P == 2) ? (A)isc[jf] : A(1), sb = (P == 2) ? (A)isc[jb] : A(1);
+      const char *uf = lbuf[mu & 1][0], *ub = lbuf[mu & 1][1];
       switch (mu) {
         case 0:
-          hop_dir_smem<D, REAL, P, 0, false, S>(acc, in, Vh, jf, su[0], s, -sg, sf);
-          hop_dir_smem<D, REAL, P, 0, true, S>(acc, in, Vh, jb, su[1], s, sg, sb);
+          hop_dir_staged<D, REAL, P, 0, false, S>(acc, in, Vh, jf, uf, s, -sg, sf);
+          hop_dir_staged<D, REAL, P, 0, true, S>(acc, in, Vh, jb, ub, s, sg, sb);
           break;
         case 1:
-          hop_dir_smem<D, REAL, P, 1, false, S>(acc, in, Vh, jf, su[0], s, -sg, sf);
-          hop_dir_smem<D, REAL, P, 1, true, S>(acc, in, Vh, jb, su[1], s, sg, sb);
+          hop_dir_staged<D, REAL, P, 1, false, S>(acc, in, Vh, jf, uf, s, -sg, sf);
+          hop_dir_staged<D, REAL, P, 1, true, S>(acc, in, Vh, jb, ub, s, sg, sb);
           break;
         case 2:
-          hop_dir_smem<D, REAL, P, 2, false, S>(acc, in, Vh, jf, su[0], s, -sg, sf);
-          hop_dir_smem<D, REAL, P, 2, true, S>(acc, in, Vh, jb, su[1], s, sg, sb);
+          hop_dir_staged<D, REAL, P, 2, false, S>(acc, in, Vh, jf, uf, s, -sg, sf);
+          hop_dir_staged<D, REAL, P, 2, true, S>(acc, in, Vh, jb, ub, s, sg, sb);
           break;
         default:
-          hop_dir_smem<D, REAL, P, 3, false, S>(acc, in, Vh, jf, su[0], s, -sg, sf);
-          hop_dir_smem<D, REAL, P, 3, true, S>(acc, in, Vh, jb, su[1], s, sg, sb);
+          hop_dir_staged<D, REAL, P, 3, false, S>(acc, in, Vh, jf, uf, s, -sg, sf);
+          hop_dir_staged<D, REAL, P, 3, true, S>(acc, in, Vh, jb, ub, s, sg, sb);
           break;
       }
     }
+    __syncthreads();  // buffer mu & 1 is refilled two directions later
   }
+  cp_async_wait<0>();
+  __syncthreads();
   if (!active) return;
-  // ---- epilogue (as hop_site) ----
+  // ---- epilogue (as hop_site, clover from shared memory) ----
   const A coef = (A)k.coef;
 #pragma unroll
   for (int c = 0; c < D; ++c)
 #pragma unroll
     for (int r = 0; r < 4; ++r) acc[c][r] = scale(coef, acc[c][r]);
   if (k.mode == HOP_SCALED) {
-    if (k.clover) clover_apply<D, P>(k.clover, Vh, i, acc);
+    if (CLOVER) clover_apply_staged<D, P, S>(cbuf, s, acc);
   } else {
     const void *self = reinterpret_cast<const char *>(k.self) + roff;
     const A ssc = (P == 2) ? (A)f16_scales(self, Vh, D)[i] : A(1);
@@ -171,8 +244,8 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) sv[c][r] = scale(ssc, sv[c][r]);
     }
-    if (k.clover) {
-      clover_apply<D, P>(k.clover, Vh, i, sv);
+    if (CLOVER) {
+      clover_apply_staged<D, P, S>(cbuf, s, sv);
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -214,29 +287,34 @@ int launch_mrhs_t(const HopK &k, cudaStream_t st) {
   const int R = (k.nrhs < 256 / S) ? k.nrhs : 256 / S;
   const int nrb = (k.nrhs + R - 1) / R;
   const int64_t tiles = (k.Vh + S - 1) / S;
-  hop_mrhs_kernel<D, REAL, P, S><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, R);
+  if (k.clover) hop_mrhs_kernel<D, REAL, P, S, true><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, R);
+  else hop_mrhs_kernel<D, REAL, P, S, false><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, R);
   return hr_check_launch("hop_mrhs_kernel");
 }
 
-// Multi-rhs launch for the one-site-per-thread classes (d_R <= 8), S sites per block.
+// S sites per block: 16 (8 for FP64, whose chunks are twice as large), and
+// half that for d_R = 8, whose staged links and clover blocks are larger.
+template <int D, bool REAL, int P>
+int mrhs_pick(const HopK &k, cudaStream_t st, int S) {
+  constexpr int SMAX = (D == 8) ? (P == 0 ? 4 : 8) : (P == 0 ? 8 : 16);
+  if (S >= SMAX) return launch_mrhs_t<D, REAL, P, SMAX>(k, st);
+  return launch_mrhs_t<D, REAL, P, (SMAX >= 8 ? SMAX / 2 : SMAX)>(k, st);
+}
+
+// Multi-rhs launch for the one-site-per-thread classes (d_R <= 8).
 template <int P>
 int hop_mrhs_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int S) {
   const HopK k = make_hopk(lat, a);
   const int d = lat->d;
-#define MR(DD, RR)                                                  \
-  return (S == 8) ? launch_mrhs_t<DD, RR, P, 8>(k, st)              \
-                  : (S == 16 ? launch_mrhs_t<DD, RR, P, 16>(k, st)  \
-                             : launch_mrhs_t<DD, RR, P, 32>(k, st))
   if (lat->is_real) {
-    if (d == 3) MR(3, true);
-    if (d == 8) MR(8, true);
+    if (d == 3) return mrhs_pick<3, true, P>(k, st, S);
+    if (d == 8) return mrhs_pick<8, true, P>(k, st, S);
   } else {
-    if (d == 2) MR(2, false);
-    if (d == 3) MR(3, false);
-    if (d == 4) MR(4, false);
-    if (d == 5) MR(5, false);
-    if (d == 6) MR(6, false);
+    if (d == 2) return mrhs_pick<2, false, P>(k, st, S);
+    if (d == 3) return mrhs_pick<3, false, P>(k, st, S);
+    if (d == 4) return mrhs_pick<4, false, P>(k, st, S);
+    if (d == 5) return mrhs_pick<5, false, P>(k, st, S);
+    if (d == 6) return mrhs_pick<6, false, P>(k, st, S);
   }
-#undef MR
   return HR_ERR_UNSUPPORTED;
 }

@@ -11,7 +11,8 @@
 //      memory (double-buffered per neighbour);
 //   2. after one warp barrier every thread multiplies its rows of U_R (or
 //      columns, for U_R^+) with the full half-spinor read back from shared
-//      memory (a broadcast within the group) and rebuilds its 4 spin rows.
+//      memory (a broadcast within the group; colour outer, rows inner, so each
+//      staged value is read once per thread) and rebuilds its 4 spin rows.
 // Groups are aligned inside a warp (G divides 32), so only __syncwarp is used.
 // Global loads stay coalesced: one load instruction covers 32/G consecutive
 // sites for each of G chunk arrays.  No clover epilogue (clover is built for
@@ -102,35 +103,43 @@ __device__ __forceinline__ void hop_split_tile(const HopK &k, int64_t tile, int 
     const void *lk = reinterpret_cast<const char *>(k.links) +
                      (size_t)(((bwd ? 1 - p : p) * 4 + mu) * slab) * es;
     const int64_t li = bwd ? j : ii;
+    // colour outer, this thread's rows inner: each staged h[c] is read once
+    cx<A> r0[R], r1[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int a = g + r * G;
-      if (a < D) {
-        cx<A> r0 = mk(A(0), A(0)), r1 = mk(A(0), A(0));
-#pragma unroll 7
-        for (int c = 0; c < D; ++c) {
-          const cx<A> h0 = hs[2 * c], h1 = hs[2 * c + 1];
+    for (int r = 0; r < R; ++r) r0[r] = r1[r] = mk(A(0), A(0));
+#pragma unroll 5
+    for (int c = 0; c < D; ++c) {
+      const cx<A> h0 = hs[2 * c], h1 = hs[2 * c + 1];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int a = g + r * G;
+        if (a < D) {
           if (REAL) {
             const int e = bwd ? (c * D + a) : (a * D + c);
             const cx<A> pr = ld2<P>(lk, (int64_t)(e >> 1) * Vh + li);
             const A ue = (e & 1) ? pr.y : pr.x;
-            r0 = rfma(ue, h0, r0);
-            r1 = rfma(ue, h1, r1);
+            r0[r] = rfma(ue, h0, r0[r]);
+            r1[r] = rfma(ue, h1, r1[r]);
           } else if (bwd) {
             const cx<A> ue = ld2<P>(lk, (int64_t)(c * D + a) * Vh + li);
-            r0 = cfmac(ue, h0, r0);
-            r1 = cfmac(ue, h1, r1);
+            r0[r] = cfmac(ue, h0, r0[r]);
+            r1[r] = cfmac(ue, h1, r1[r]);
           } else {
             const cx<A> ue = ld2<P>(lk, (int64_t)(a * D + c) * Vh + li);
-            r0 = cfma(ue, h0, r0);
-            r1 = cfma(ue, h1, r1);
+            r0[r] = cfma(ue, h0, r0[r]);
+            r1[r] = cfma(ue, h1, r1[r]);
           }
         }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (g + r * G < D) {
         switch (mu) {
-          case 0: reconstruct<0>(sig, r0, r1, acc[r]); break;
-          case 1: reconstruct<1>(sig, r0, r1, acc[r]); break;
-          case 2: reconstruct<2>(sig, r0, r1, acc[r]); break;
-          default: reconstruct<3>(sig, r0, r1, acc[r]); break;
+          case 0: reconstruct<0>(sig, r0[r], r1[r], acc[r]); break;
+          case 1: reconstruct<1>(sig, r0[r], r1[r], acc[r]); break;
+          case 2: reconstruct<2>(sig, r0[r], r1[r], acc[r]); break;
+          default: reconstruct<3>(sig, r0[r], r1[r], acc[r]); break;
         }
       }
     }

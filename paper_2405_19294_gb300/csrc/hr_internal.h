@@ -46,6 +46,7 @@ struct hr_lattice {
   void *clover_term;     // FP64 packed blocks of csw (i/4) sigma.F (no mass term)
   double clover_m0;      // m0 of the cached A and A^{-1} below
   int clover_cached;
+  int clover_exp;         // 1: A = (4+m0) exp(term / (4+m0)) (exponentiated clover)
   void *clover_A[2];     // FP64, FP32 packed A = (4+m0) + term
   void *clover_Ainv[2];  // FP64, FP32 packed A^{-1}
   void *tmp;             // Schur intermediate spinor (other parity)

@@ -25,7 +25,6 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
     // links staged once per site for all right-hand sides of a block
     out[n++] = HopShape{0, 0, 0, 16};
     out[n++] = HopShape{0, 0, 0, 8};
-    out[n++] = HopShape{0, 0, 0, 32};
   }
   if (site) {
     // compiler's register choice at 64 / 128 / 32 / 256 threads, then (not
@@ -125,7 +124,7 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 }
 
 // Report the tuned shape for the lattice's hop at (prec, nrhs, clover): returns
-// mrhs * 100000 + regs * 10000 + split_g * 1000 + block size, or -1 if not tuned yet.
+// mrhs * 10000000 + regs * 1000000 + split_g * 1000 + block size, or -1 if not tuned yet.
 extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover) {
   if (!lat) return -1;
   HopArgs a;
@@ -135,7 +134,7 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_best.find(tune_key(lat, prec, a));
   if (it == g_best.end()) return -1;
-  return it->second.mrhs * 100000 + it->second.regs * 10000 + it->second.split_g * 1000 + it->second.bs;
+  return it->second.mrhs * 10000000 + it->second.regs * 1000000 + it->second.split_g * 1000 + it->second.bs;
 }
 
 // Candidate shapes of this lattice's hop, encoded as hr_tuned_shape reports them.
@@ -144,7 +143,7 @@ extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n && k < max; ++k)
-    out[k] = shapes[k].mrhs * 100000 + shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs;
+    out[k] = shapes[k].mrhs * 10000000 + shapes[k].regs * 1000000 + shapes[k].split_g * 1000 + shapes[k].bs;
   return n;
 }
 
@@ -155,7 +154,7 @@ extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n; ++k)
-    if (shapes[k].mrhs * 100000 + shapes[k].regs * 10000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
+    if (shapes[k].mrhs * 10000000 + shapes[k].regs * 1000000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
       HopArgs a;
       memset(&a, 0, sizeof(a));
       a.nrhs = nrhs;

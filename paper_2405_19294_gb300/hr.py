@@ -55,6 +55,7 @@ _SIGS = {
     "hr_represent_links": (C.c_int, [_P, _P, C.c_int, C.c_double]),
     "hr_export_represented_links": (C.c_int, [_P, _P]),
     "hr_export_clover": (C.c_int, [_P, _P, C.c_double, C.c_int]),
+    "hr_set_clover_exponential": (C.c_int, [_P, C.c_int]),
     "hr_pack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int]),
     "hr_unpack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int]),
     "hr_dphi": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
@@ -71,6 +72,8 @@ _SIGS = {
     "hr_batch_dphi": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int]),
     "hr_batch_cg_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(hr_cg_params), C.POINTER(hr_cg_stats)]),
+    "hr_bicgstab_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
+                                    C.POINTER(hr_cg_stats)]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -179,6 +182,10 @@ class Lattice:
     def export_clover(self, out, m0: float, inverse: bool = False):
         _check(_lib.hr_export_clover(self._h, _ptr(out), m0, int(inverse)), "hr_export_clover")
 
+    def set_clover_exponential(self, on: bool = True):
+        """A = (4 + m0) exp(C / (4 + m0)) instead of (4 + m0) + C for later calls."""
+        _check(_lib.hr_set_clover_exponential(self._h, int(bool(on))), "hr_set_clover_exponential")
+
     # -- operator and solver ---------------------------------------------
     def dphi(self, out, inp, parity: int, m0: float, csw: float, prec: int, nrhs: int = 1,
              dagger: bool = False):
@@ -187,7 +194,7 @@ class Lattice:
 
     @staticmethod
     def _decode(v):
-        return ((v % 10000) // 1000, v % 1000, (v % 100000) // 10000, v // 100000)
+        return ((v % 1000000) // 1000, v % 1000, (v % 10000000) // 1000000, v // 10000000)
 
     def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
         """(G threads per site or 0, threads per block, register budget, multi-rhs sites per block)
@@ -205,7 +212,7 @@ class Lattice:
     def set_shape(self, prec: int, shape, nrhs: int = 1, clover: bool = False):
         g, bs, regs = shape[0], shape[1], shape[2]
         mr = shape[3] if len(shape) > 3 else 0
-        code = mr * 100000 + regs * 10000 + g * 1000 + bs
+        code = mr * 10000000 + regs * 1000000 + g * 1000 + bs
         _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), code), "hr_set_tuned_shape")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
@@ -268,6 +275,21 @@ class Batch:
             raise HrError(rc, "hr_batch_cg_solve")
         return rc, [{"iterations": s.iterations, "outer_steps": s.outer_steps, "true_residual": s.true_residual,
                      "seconds": s.seconds} for s in st]
+
+
+def _bicgstab(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
+              inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,
+              raise_on_error: bool = True):
+    prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every)
+    st = hr_cg_stats()
+    rc = _lib.hr_bicgstab_solve(self._h, _ptr(x), _ptr(b), parity, m0, csw, C.byref(prm), C.byref(st))
+    if rc != 0 and raise_on_error:
+        raise HrError(rc, "hr_bicgstab_solve")
+    return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
+            "true_residual": st.true_residual, "seconds": st.seconds}
+
+
+Lattice.bicgstab_solve = _bicgstab
 
 
 def lib_handle():

@@ -27,9 +27,10 @@ def oracle_links(T, L, N, eps, seed=0, reunitarise=True):
     return sun.reunitarise(U) if reunitarise else U
 
 
-def oracle_operator(T, L, N, rep, eps, m0, csw, seed=0):
+def oracle_operator(T, L, N, rep, eps, m0, csw, seed=0, exponential=False):
     g = Geometry(T, L)
-    return WilsonOperator(oracle_links(T, L, N, eps, seed), N, rep, g, m0, csw)
+    return WilsonOperator(oracle_links(T, L, N, eps, seed), N, rep, g, m0, csw,
+                          exponential=exponential)
 
 
 def to_complex(t):

@@ -1,0 +1,92 @@
+"""Exponentiated clover term (Sec. 3.1; Francis, Fritzsch, Luscher and Rago):
+A = (4 + m0) exp(C / (4 + m0)) built on the GPU against the oracle's scipy
+expm of the full 4d x 4d matrix -- the exported blocks and their inverses, the
+operator in all three precisions and both parities, and a CG solve."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, from_complex, gpu_lattice, oracle_operator, rel_err, to_complex
+from paper_2405_19294_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [(2, "fund"), (3, "fund"), (3, "sym"), (2, "adj"), (4, "asym"), (3, "adj")]
+
+
+@pytest.mark.parametrize("N,rep", CASES)
+def test_exp_clover_blocks(hr, N, rep):
+    T, L, m0, csw = 4, 4, -0.35, 1.3
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, csw)
+    lat.set_clover_exponential(True)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, csw, exponential=True)
+    d = lat.d
+    A = torch.empty((lat.V, 2, 2 * d, 2 * d, 2), dtype=torch.float64, device="cuda")
+    lat.export_clover(A, m0, inverse=False)
+    Ag = to_complex(A)
+    for b in range(2):
+        blk = op.A[:, 2 * b * d:(2 * b + 2) * d, 2 * b * d:(2 * b + 2) * d]
+        assert np.max(np.abs(Ag[:, b] - blk)) < 1e-12 * np.max(np.abs(blk))
+    lat.export_clover(A, m0, inverse=True)
+    Ig = to_complex(A)
+    for b in range(2):
+        blk = op.A[:, 2 * b * d:(2 * b + 2) * d, 2 * b * d:(2 * b + 2) * d]
+        inv = np.linalg.inv(blk)
+        assert np.max(np.abs(Ig[:, b] - inv)) < 1e-12 * np.max(np.abs(inv))
+    # switching back restores the plain Sheikholeslami-Wohlert term
+    lat.set_clover_exponential(False)
+    lat.export_clover(A, m0, inverse=False)
+    plain = oracle_operator(T, L, N, rep, 1.0, m0, csw)
+    assert np.max(np.abs(to_complex(A)[:, 0] - plain.A[:, :2 * d, :2 * d])) < 1e-13
+
+
+def _gpu_apply(lat, psi, parity, m0, csw, prec, dagger):
+    fin = lat.new_field(parity, prec, 1)
+    fout = lat.new_field(parity, prec, 1)
+    lat.pack(fin, from_complex(psi), parity, prec, 1)
+    lat.dphi(fout, fin, parity, m0, csw, prec, 1, dagger)
+    out = torch.zeros((1, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, fout, parity, prec, 1)
+    lat.synchronize()
+    return to_complex(out)[0]
+
+
+@pytest.mark.parametrize("N,rep", CASES)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_exp_clover_dphi_parity(hr, N, rep, prec):
+    T, L, m0, csw = 6, 4, -0.35, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, csw)
+    lat.set_clover_exponential(True)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, csw, exponential=True)
+    psi = inputs.gaussian_spinor(2, T, L, lat.d)[0]
+    g = op.geom
+    for parity in (0, 1, 2):
+        for dagger in (0, 1):
+            got = _gpu_apply(lat, psi, parity, m0, csw, prec, dagger)
+            ref = op.apply(psi, dagger=bool(dagger)) if parity == 2 else \
+                op.apply_schur(psi, parity, dagger=bool(dagger))
+            mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+            assert rel_err(got, ref, mask) < TOL[prec], (parity, dagger)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exp_clover_cg(hr, prec):
+    """CG on Dhat^+ Dhat with the exponentiated term: true FP64 residual of the oracle's operator."""
+    T, L, N, rep, m0, csw = 8, 4, 3, "fund", -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, csw)
+    lat.set_clover_exponential(True)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, csw, exponential=True)
+    g = op.geom
+    b = inputs.gaussian_spinor(4, T, L, lat.d)[0]
+    b = np.where((g.parity == 0)[:, None, None], b, 0)
+    fb = lat.new_field(0, 0, 1)
+    fx = lat.new_field(0, 0, 1)
+    lat.pack(fb, from_complex(b), 0, 0, 1)
+    res = lat.cg_solve(fx, fb, 0, m0, csw, 1e-10, inner_prec=prec)
+    out = torch.zeros((1, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, fx, 0, 0, 1)
+    lat.synchronize()
+    x = to_complex(out)[0]
+    r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10, res

@@ -69,3 +69,36 @@ def test_cg_normal_equations_true_residual():
     assert res <= 1e-10
     # odd sites stay untouched by the even Schur operator
     assert np.all(x[g.parity == 1] == 0)
+
+
+@pytest.mark.parametrize("csw", [0.0, 1.0])
+def test_bicgstab_schur_matches_lapack(csw):
+    """BiCGstab on Dhat_e x = b directly reproduces the dense solution of the Schur system."""
+    g, op, b = _setup(3, "fund", 4, 4, 1.0, -0.35, csw)
+    ev = g.parity == 0
+    be = np.where(ev[:, None, None], b, 0)
+    A = lambda v: op.apply_schur(v, 0)
+    x, it, res = solvers.bicgstab(A, be, 1e-10)
+    assert res <= 1e-10
+    Dm = _dense(lambda v: op.apply_schur(v, 0), g.V, op.d)
+    n = 4 * op.d
+    mask = np.repeat(ev, n)
+    xd = scipy.linalg.solve(Dm[np.ix_(mask, mask)], be.ravel()[mask])
+    assert np.linalg.norm(x.ravel()[mask] - xd) / np.linalg.norm(xd) < 1e-8
+    # fewer operator applications than CG on the normal equations
+    M = lambda v: op.apply_schur(op.apply_schur(v, 0), 0, dagger=True)
+    rhs = op.apply_schur(be, 0, dagger=True)
+    _, it_cg, _ = solvers.cg(M, rhs, 1e-10)
+    assert 2 * it <= 2 * it_cg + 4
+
+
+def test_bicgstab_nonhermitian_small_dense():
+    """A random well-conditioned non-Hermitian matrix: BiCGstab against LAPACK."""
+    rng = np.random.default_rng(33)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A *= 0.5
+    bb = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, res = solvers.bicgstab(lambda v: A @ v, bb, 1e-12)
+    assert res <= 1e-12
+    assert np.allclose(x, np.linalg.solve(A, bb), atol=1e-9)

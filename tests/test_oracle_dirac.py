@@ -308,3 +308,37 @@ def test_lazy_evaluation_matches_eager():
         ref = eager.apply_schur(psi, 1, dagger=dag)
         got = lazy.apply_schur(psi, 1, dagger=dag, sites=sites)
         assert np.max(np.abs(got[sites] - ref[sites])) < 1e-13
+
+
+@pytest.mark.parametrize("N,rep", [(2, "fund"), (3, "sym"), (2, "adj")])
+def test_exponentiated_clover(N, rep):
+    """A = (4+m0) exp(C/(4+m0)): Hermitian, commutes with gamma_5, positive, inverse by -C,
+    first-order agreement with the standard clover term, gauge covariant."""
+    T, L, m0 = 4, 4, -0.35
+    g = Geometry(T, L)
+    d = sun.rep_dim(N, rep)
+    U = _links(N, T, L, 1.0, 30)
+    c = 4 + m0
+    op_e = WilsonOperator(U, N, rep, g, m0, 1.0, exponential=True)
+    op_s = WilsonOperator(U, N, rep, g, m0, 1.0)
+    A = op_e.A
+    assert np.allclose(A, np.conj(np.swapaxes(A, 1, 2)), atol=1e-12)
+    G5 = np.kron(GAMMA5, np.eye(d))
+    assert np.allclose(G5 @ A, A @ G5, atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(A) > 0)                 # exp of Hermitian: positive definite
+    C = op_s.A - c * np.eye(4 * d)
+    import scipy.linalg
+    for x in (0, 17, 100):
+        Ainv = scipy.linalg.expm(-C[x] / c) / c
+        assert np.allclose(A[x] @ Ainv, np.eye(4 * d), atol=1e-12)
+        # eigenvalues are c exp(lambda / c) of C's eigenvalues lambda
+        lam = np.linalg.eigvalsh(C[x])
+        assert np.allclose(np.sort(np.linalg.eigvalsh(A[x])), np.sort(c * np.exp(lam / c)), atol=1e-11)
+    # small c_sw: exponentiated and standard agree to first order, differ at second
+    small_e = WilsonOperator(U, N, rep, g, m0, 1e-3, exponential=True).A
+    small_s = WilsonOperator(U, N, rep, g, m0, 1e-3).A
+    diff = np.max(np.abs(small_e - small_s))
+    assert 0 < diff < 1e-5
+    # trivial field: no clover term either way
+    U1 = np.broadcast_to(np.eye(N, dtype=complex), U.shape).copy()
+    assert np.allclose(WilsonOperator(U1, N, rep, g, m0, 1.0, exponential=True).A, c * np.eye(4 * d), atol=1e-13)
