@@ -294,7 +294,78 @@ def run_suite(args):
         out.append(_suite_c3(hr, inputs, torch))
     if "c4" in which:
         out.append(_suite_c4(hr, inputs, torch))
+    if "largen" in which:
+        out.extend(_suite_large_nc(hr, inputs, torch))
     return out
+
+
+def _large_nc_geometry(N, target_bytes):
+    """L^3 x T, T in {L, 3L/2, 2L} (both even), whose FP32 Dhat moves closest to target_bytes."""
+    bps = bytes_per_even_site(N, "fund", 4)
+    want = target_bytes / bps * 2          # sites of the full lattice
+    best = None
+    for L in range(4, 130, 2):
+        for T in (L, 3 * L // 2, 2 * L):
+            if T % 2:
+                continue
+            err = abs(T * L ** 3 - want) / want
+            if best is None or err < best[0]:
+                best = (err, T, L)
+    return best[1], best[2]
+
+
+def _time_dhat(lat, fi, fo, m0, prec, torch, flush, reps=10):
+    for _ in range(2):
+        lat.dphi(fo, fi, 0, m0, 0.0, prec)
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.sum()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lat.dphi(fo, fi, 0, m0, 0.0, prec)
+        e1.record(st)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+
+def _suite_large_nc(hr, inputs, torch):
+    """Large-N_c scaling (Sec. 3.1.2): SU(N_c) fundamental, N_c = 2 ... 12, FP32
+    Dhat, the lattice shrunk as N_c grows so that every point moves about the
+    same bytes; every launch shape timed, grouped into the one-site-per-thread
+    kernel (the paper's default) and the kernels split over the colour rows
+    (its LARGE_N kernel: here the rows and colour-split kernels)."""
+    m0, prec = -0.3, hr.F32
+    flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+    lines = []
+    for N in range(2, 13):
+        T, L = _large_nc_geometry(N, 2.0e9)
+        lat = _lattice(hr, inputs, torch, T, L, N, "fund", 1.0, 0.0)
+        fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
+        fo = lat.new_field(0, prec)
+        bytes_ = bytes_per_even_site(N, "fund", 4) * lat.Vh
+        flops = flops_per_even_site(N, "fund") * lat.Vh
+        shapes = {}
+        for sh in lat.shape_candidates(prec):
+            lat.set_shape(prec, sh)
+            ms = _time_dhat(lat, fi, fo, m0, prec, torch, flush)
+            fam = "site" if (sh[0] == 0 and sh[4] == 0) else ("rows" if sh[4] else "split")
+            shapes[str(tuple(sh))] = {"family": fam, "ms": round(ms, 4),
+                                      "GBs": round(bytes_ / ms / 1e6, 1), "GFLOPs": round(flops / ms / 1e6, 1)}
+        best = {}
+        for k, v in shapes.items():
+            if v["family"] not in best or v["ms"] < best[v["family"]]["ms"]:
+                best[v["family"]] = dict(v, shape=k)
+        line = {"suite": "large-N_c scaling, SU(N_c) fund, FP32 Dhat, ~2 GB moved per application",
+                "N_c": N, "lattice": f"{L}^3x{T}", "even_sites": lat.Vh, "model_bytes": int(bytes_),
+                "model_flops": int(flops), "best_per_family": best, "shapes": shapes}
+        print(json.dumps(line), flush=True)
+        lines.append(line)
+        lat.close()
+        del fi, fo
+        torch.cuda.empty_cache()
+    return lines
 
 
 def _suite_bicgstab(hr, inputs, torch):
@@ -413,7 +484,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4: measure those workloads instead")
+    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen: measure those workloads instead")
     ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
@@ -556,7 +627,7 @@ def main():
     roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(gbs / world / peaks["hbm_gbs"], 4), "peak_kind": kind,
             "traffic": (round(traffic * sites / 2) if traffic else None),
-            "kernel": f"hop_kernel<3,false,{TP}>, tuned shape (G, block, regs, mrhs) = {lat.tuned_shape(TP)}, "
+            "kernel": f"hop_kernel<3,false,{TP}>, tuned shape (G, block, regs, mrhs, rows) = {lat.tuned_shape(TP)}, "
                       "2 launches per Dhat"}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,

@@ -98,8 +98,9 @@ typedef struct {
 /* ---- lattice handle --------------------------------------------------- */
 
 /* Create a T x L^3 lattice for SU(N) fermions in representation rep on the
- * current CUDA device.  T, L even and >= 2; 2 <= N <= 6; (N=2, ASYM) is the
- * trivial singlet and is rejected.  Allocates nothing large until links are
+ * current CUDA device.  T, L even and >= 2; 2 <= N <= 12 for FUND (the
+ * large-N_c workload of Sec. 3.1.2), 2 <= N <= 6 for ADJ, SYM, ASYM; (N=2,
+ * ASYM) is the trivial singlet and is rejected.  Allocates nothing large until links are
  * loaded.  Errors: HR_ERR_ARG.  (Sec. 3.1: any N_c and representation.) */
 int hr_lattice_create(int T, int L, int N, int rep, hr_lattice **out);
 
@@ -246,6 +247,12 @@ int hr_batch_destroy(hr_batch *batch);
 /* Stream the batch's work is ordered after (default: the first lattice's). */
 int hr_batch_set_stream(hr_batch *batch, void *cuda_stream);
 
+/* Pin the hopping launch shape of the class (d_R = d, real links is_real) at
+ * precision prec instead of timing its candidates.  `shape` is one of the
+ * codes hr_hop_shape_candidates reports for such a lattice (nrhs = 1, no
+ * clover).  Errors: HR_ERR_ARG (no such class or shape). */
+int hr_batch_set_shape(hr_batch *batch, int d, int is_real, int prec, int shape);
+
 /* out[i] = Dhat_p in[i] (or its adjoint) on lattice i, parity EVEN or ODD,
  * bare mass m0[i] (host array); internal single-parity fields of precision
  * prec, one rhs each.  The first call per precision times each class's
@@ -265,9 +272,11 @@ int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int
                       const hr_cg_params *params, hr_cg_stats *stats);
 
 /* The hopping-kernel launch shape the autotuner chose for this lattice at
- * (prec, nrhs, clover): mrhs * 10000000 + regs * 1000000 + split_g * 1000 +
- * threads per block.  mrhs = S > 0: the multi-right-hand-side kernel with S
- * sites per block (links staged once per site for all right-hand sides);
+ * (prec, nrhs, clover): rows * 100000000 + mrhs * 1000000 + regs * 100000 +
+ * split_g * 1000 + threads per block.  mrhs = S > 0: the multi-right-hand-
+ * side kernel with S sites per block (links staged once per site for all
+ * right-hand sides); rows = R > 0: the rows kernel for large d_R (R output
+ * colour rows per warp, 32 sites per block on the lanes); otherwise
  * split_g = 0: one site per thread with register budget regs = 0 compiler's
  * choice, 1 up to ~170, 2 at most ~85 registers; split_g = G > 0: G threads
  * per site.  -1 if not tuned yet.  The

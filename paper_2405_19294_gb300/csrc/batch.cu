@@ -136,7 +136,7 @@ static double *BS(hr_batch *b, int k) { return b->scal + (size_t)k * b->n; }
 
 static int build_items(BClass &c, const std::vector<hr_lattice *> &lats, int prec) {
   const HopShape sh = c.sh[prec];
-  const int tile = sh.split_g ? 128 / sh.split_g : sh.bs;
+  const int tile = hr_shape_tile(sh);
   std::vector<int2> items;
   for (int li : c.members) {
     const int64_t nt = (lats[li]->Vh + tile - 1) / tile;
@@ -334,6 +334,25 @@ static int tune_classes(hr_batch *b, int prec, int slot0, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return HR_OK;
+}
+
+// Pin the launch shape of the class (d, is_real) at precision prec instead of
+// timing its candidates; the shape must be one of them.
+extern "C" int hr_batch_set_shape(hr_batch *b, int d, int is_real, int prec, int shape) {
+  if (!b || prec < HR_F64 || prec > HR_F16) return HR_ERR_ARG;
+  for (auto &c : b->cls) {
+    if (c.d != d || c.is_real != (is_real != 0)) continue;
+    HopShape shapes[HR_MAX_SHAPES];
+    const int ns = hr_hop_shapes(c.d, c.is_real, prec, 0, 0, shapes);
+    for (int k = 0; k < ns; ++k)
+      if (hr_shape_code(shapes[k]) == shape) {
+        c.sh[prec] = shapes[k];
+        c.tuned[prec] = 1;
+        return build_items(c, b->lats, prec);
+      }
+    return HR_ERR_ARG;
+  }
+  return HR_ERR_ARG;
 }
 
 // launches of one batched Dhat (stages slot0, slot0+1 of d_desc)

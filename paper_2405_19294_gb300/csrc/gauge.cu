@@ -28,8 +28,8 @@ __device__ __forceinline__ zd zconj(zd a) { return mk(a.x, -a.y); }
 // nonzero entries of generator T_a of su(N): count, rows, cols, values
 struct GenNZ {
   int n;
-  int r[6], c[6];
-  zd v[6];
+  int r[HR_MAX_NC], c[HR_MAX_NC];
+  zd v[HR_MAX_NC];
 };
 
 __device__ void generator_nz(int N, int a, GenNZ &g) {
@@ -113,6 +113,7 @@ __device__ zd det_lu(zd *M, int N) {
 }
 
 // rows Gram-Schmidt (modified), then last row times conj(det)
+template <int NM>
 __device__ void reunitarise_dev(zd *U, int N) {
   for (int i = 0; i < N; ++i) {
     for (int j = 0; j < i; ++j) {
@@ -125,13 +126,14 @@ __device__ void reunitarise_dev(zd *U, int N) {
     const double inv = 1.0 / sqrt(n2);
     for (int c = 0; c < N; ++c) U[i * N + c] = scale(inv, U[i * N + c]);
   }
-  zd M[36];
+  zd M[NM * NM];
   for (int e = 0; e < N * N; ++e) M[e] = U[e];
   const zd dt = zconj(det_lu(M, N));
   for (int c = 0; c < N; ++c) U[(N - 1) * N + c] = zmul(U[(N - 1) * N + c], dt);
 }
 
 // ------------------------------------------------------ link generation ----
+template <int NM>
 __global__ void links_from_algebra_kernel(double *U_out, const double *a_in, double eps, int N, int64_t nlinks,
                                           int reun) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,7 +141,7 @@ __global__ void links_from_algebra_kernel(double *U_out, const double *a_in, dou
   const int ng = N * N - 1;
   const double *a = a_in + l * ng;
   // X = i eps H, H = sum_k a_k T_k
-  zd X[36];
+  zd X[NM * NM];
   for (int e = 0; e < N * N; ++e) X[e] = mk(0.0, 0.0);
   for (int k = 0; k < ng; ++k) {
     GenNZ g;
@@ -161,7 +163,7 @@ __global__ void links_from_algebra_kernel(double *U_out, const double *a_in, dou
   const double sc = ldexp(1.0, -s);
   for (int e = 0; e < N * N; ++e) X[e] = scale(sc, X[e]);
   // Taylor series to order 18: E = sum_k X^k / k!
-  zd E[36], Tm[36], W[36];
+  zd E[NM * NM], Tm[NM * NM], W[NM * NM];
   for (int e = 0; e < N * N; ++e) {
     E[e] = mk((e % (N + 1) == 0) ? 1.0 : 0.0, 0.0);
     Tm[e] = E[e];
@@ -189,7 +191,7 @@ __global__ void links_from_algebra_kernel(double *U_out, const double *a_in, dou
       }
     for (int e = 0; e < N * N; ++e) E[e] = W[e];
   }
-  if (reun) reunitarise_dev(E, N);
+  if (reun) reunitarise_dev<NM>(E, N);
   double *o = U_out + l * 2 * N * N;
   for (int e = 0; e < N * N; ++e) {
     o[2 * e] = E[e].x;
@@ -201,8 +203,11 @@ extern "C" int hr_links_from_algebra(hr_lattice *lat, double *U_dev, const doubl
                                      int reunitarise) {
   if (!lat || !U_dev || !a_dev) return HR_ERR_ARG;
   const int64_t nl = lat->V * 4;
-  links_from_algebra_kernel<<<(unsigned)((nl + 127) / 128), 128, 0, lat->stream>>>(U_dev, a_dev, eps, lat->N, nl,
-                                                                                   reunitarise);
+  const unsigned nb = (unsigned)((nl + 127) / 128);
+  if (lat->N <= 6)  // smaller per-thread scratch for the common groups
+    links_from_algebra_kernel<6><<<nb, 128, 0, lat->stream>>>(U_dev, a_dev, eps, lat->N, nl, reunitarise);
+  else
+    links_from_algebra_kernel<HR_MAX_NC><<<nb, 128, 0, lat->stream>>>(U_dev, a_dev, eps, lat->N, nl, reunitarise);
   return hr_check_launch("links_from_algebra_kernel");
 }
 
@@ -239,16 +244,17 @@ __device__ zd rep_entry(const zd *U, int N, int rep, int ra, int rb) {
   return scale(nab * ncd, t1 + t2);
 }
 
+template <int NM>
 __global__ void represent_kernel(void *l64, void *l32, void *l16, const double *U_in, RepK k) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= k.V * 4) return;
   const int64_t x = l >> 2;
   const int mu = (int)(l & 3);
   const int N = k.N, d = k.d;
-  zd U[36];
+  zd U[NM * NM];
   const double *src = U_in + l * 2 * N * N;
   for (int e = 0; e < N * N; ++e) U[e] = mk(src[2 * e], src[2 * e + 1]);
-  if (k.reun) reunitarise_dev(U, N);
+  if (k.reun) reunitarise_dev<NM>(U, N);
   // coordinates from the lexicographic index
   const int xx = (int)(x % k.L);
   const int yy = (int)((x / k.L) % k.L);
@@ -301,8 +307,12 @@ extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reun
   k.V = lat->V;
   k.Vh = lat->Vh;
   const int64_t nl = lat->V * 4;
-  represent_kernel<<<(unsigned)((nl + 63) / 64), 64, 0, lat->stream>>>(lat->links[0], lat->links[1], lat->links[2],
-                                                                       U_dev, k);
+  if (lat->N <= 6)
+    represent_kernel<6><<<(unsigned)((nl + 63) / 64), 64, 0, lat->stream>>>(lat->links[0], lat->links[1],
+                                                                          lat->links[2], U_dev, k);
+  else
+    represent_kernel<HR_MAX_NC><<<(unsigned)((nl + 63) / 64), 64, 0, lat->stream>>>(lat->links[0], lat->links[1],
+                                                                                  lat->links[2], U_dev, k);
   HR_TRY(hr_check_launch("represent_kernel"));
   lat->have_links = 1;
   lat->csw = csw;

@@ -371,6 +371,8 @@ int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int b
       case 4: launch_site<4, false, P>(k, grid, bs, variant, st); break;
       case 5: launch_site<5, false, P>(k, grid, bs, variant, st); break;
       case 6: launch_site<6, false, P>(k, grid, bs, variant, st); break;
+      case 7: launch_site<7, false, P>(k, grid, bs, variant, st); break;
+      case 8: launch_site<8, false, P>(k, grid, bs, variant, st); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   }

@@ -3,11 +3,13 @@
 // colour-split groups (hop_split.cuh) for d_R >= 6;
 // the autotuner in tune.cu chooses among the shapes listed by hr_hop_shapes.
 #include "hop_mrhs.cuh"
+#include "hop_rows.cuh"
 #include "hop_split.cuh"
 
 int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh) {
   const int d = lat->d;
   if (sh.mrhs > 0) return hop_mrhs_dispatch<0>(lat, a, s, sh.mrhs);
+  if (sh.rows > 0) return rows_dispatch<0>(lat, a, s, sh.rows);
   if (sh.split_g == 0) return hop_dispatch<0>(lat, a, s, sh.bs, sh.regs);
   if (a.clover) return HR_ERR_UNSUPPORTED;
   const HopK k = make_hopk(lat, a);

@@ -1,0 +1,303 @@
+// Hopping kernel for large representations with the output colour rows of
+// U_R x half-spinor spread over the warps of a block and 32 consecutive sites
+// over the lanes of each warp.
+//
+// Sec. 3.1.2 of the paper parallelises the represented-link product in the
+// representation dimension once a one-site-per-thread kernel runs out of
+// registers.  The colour-split kernel (hop_split.cuh) keeps a site's G threads
+// inside one warp, so one warp-wide link load touches G separate chunk rows of
+// 32/G sites each.  Here every warp instead owns R consecutive output rows
+// a = w R ... w R + R - 1 for the same 32 sites, so every link load of a warp
+// reads one chunk row for 32 consecutive sites (256 B in FP32, fully
+// coalesced).  For each of the 8 neighbours:
+//   1. warp w loads colours c = w R ... of psi(j) for its 32 sites, projects
+//      them (Sec. 2.2) and stores h0[c], h1[c] to shared memory laid out
+//      [colour][lane] (double-buffered per neighbour);
+//   2. one block barrier; then each warp multiplies its R rows of U_R (or
+//      columns of U_R, for U_R^+) with the full half-spinor of its lane's site
+//      (colour outer, rows inner) and rebuilds the 4 spin components.
+// One barrier per neighbour suffices: a warp that writes the buffer of
+// neighbour n+2 has passed the barrier of n+1, which every warp reaches only
+// after it has finished reading neighbour n.  No clover epilogue (the clover
+// term is built for d_R <= 8, where the site kernel is used).
+#pragma once
+
+#include "hop.cuh"
+
+template <int D, int R>
+struct RowsGeom {
+  static constexpr int W = (D + R - 1) / R;  // warps per block
+  static constexpr int NT = 32 * W;           // threads per block
+};
+
+// bytes of dynamic shared memory: the double-buffered half-spinors plus, for
+// FP16 output, one float per (warp, lane) for the per-site maximum
+template <int D, int R, int P>
+constexpr size_t rows_smem_bytes() {
+  return (size_t)2 * 2 * D * 32 * sizeof(cx<typename PT<P>::A>) + (P == 2 ? (size_t)RowsGeom<D, R>::W * 32 * 4 : 0);
+}
+
+// r0[r] += U[a][c] h0 (or conj(U[c][a]) h0 when ADJ), same for h1, for this
+// warp's rows a = a0 + r < D, all colours c.
+template <int D, bool REAL, int P, int R, bool ADJ>
+__device__ __forceinline__ void rows_mul(const cx<typename PT<P>::A> *hs, int lane, int a0, const void *lk,
+                                         int64_t li, int64_t Vh, cx<typename PT<P>::A> r0[R],
+                                         cx<typename PT<P>::A> r1[R]) {
+  typedef typename PT<P>::A A;
+#pragma unroll 3
+  for (int c = 0; c < D; ++c) {
+    const cx<A> h0 = hs[(2 * c) * 32 + lane], h1 = hs[(2 * c + 1) * 32 + lane];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int a = a0 + r;
+      if (a < D) {
+        const int e = ADJ ? (c * D + a) : (a * D + c);
+        if (REAL) {
+          const cx<A> pr = ld2<P>(lk, (int64_t)(e >> 1) * Vh + li);
+          const A ue = (e & 1) ? pr.y : pr.x;
+          r0[r] = rfma(ue, h0, r0[r]);
+          r1[r] = rfma(ue, h1, r1[r]);
+        } else {
+          const cx<A> ue = ld2<P>(lk, (int64_t)e * Vh + li);
+          if (ADJ) {
+            r0[r] = cfmac(ue, h0, r0[r]);
+            r1[r] = cfmac(ue, h1, r1[r]);
+          } else {
+            r0[r] = cfma(ue, h0, r0[r]);
+            r1[r] = cfma(ue, h1, r1[r]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// One tile of 32 output sites of right-hand side rhs.  Every thread of the
+// block must call it (block barriers inside).  `smem` holds rows_smem_bytes.
+template <int D, bool REAL, int P, int R>
+__device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int rhs, unsigned char *smem) {
+  typedef typename PT<P>::A A;
+  constexpr int W = RowsGeom<D, R>::W;
+  cx<A> *sh = reinterpret_cast<cx<A> *>(smem);  // [2][2D][32]
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int a0 = w * R;
+  const int64_t i = tile * 32 + lane;
+  const bool active = i < k.Vh;
+  const int64_t ii = active ? i : 0;  // inactive lanes still join the barriers
+  const size_t roff = (size_t)rhs * k.stride;
+  const void *in = reinterpret_cast<const char *>(k.in) + roff;
+  void *out = reinterpret_cast<char *>(k.out) + roff;
+  const int64_t Vh = k.Vh;
+  const int L = k.L, Lh = k.Lh, T = k.T, p = k.p;
+  const Site s = site_of(ii, p, L, Lh);
+  const A sg = (A)k.sgn;
+  const int64_t slab = (int64_t)k.nch * Vh;
+  const size_t es = (P == 0) ? 16 : (P == 1 ? 8 : 4);
+  const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
+
+  cx<A> acc[R][4];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = mk(A(0), A(0));
+
+  const int64_t LLh = (int64_t)L * Lh;
+  int64_t nb[8];
+  {
+    const int tf = (s.t + 1 == T) ? 0 : s.t + 1, tb = (s.t == 0) ? T - 1 : s.t - 1;
+    nb[0] = ii + (int64_t)(tf - s.t) * L * LLh;
+    nb[1] = ii + (int64_t)(tb - s.t) * L * LLh;
+    const int xf = (s.x + 1 == L) ? 0 : s.x + 1, xb = (s.x == 0) ? L - 1 : s.x - 1;
+    nb[2] = ii - (s.x >> 1) + (xf >> 1);
+    nb[3] = ii - (s.x >> 1) + (xb >> 1);
+    const int yf = (s.y + 1 == L) ? 0 : s.y + 1, yb = (s.y == 0) ? L - 1 : s.y - 1;
+    nb[4] = ii + (int64_t)(yf - s.y) * Lh;
+    nb[5] = ii + (int64_t)(yb - s.y) * Lh;
+    const int zf = (s.z + 1 == L) ? 0 : s.z + 1, zb = (s.z == 0) ? L - 1 : s.z - 1;
+    nb[6] = ii + (int64_t)(zf - s.z) * LLh;
+    nb[7] = ii + (int64_t)(zb - s.z) * LLh;
+  }
+
+#pragma unroll 1
+  for (int n = 0; n < 8; ++n) {
+    const int mu = n >> 1;
+    const bool bwd = n & 1;
+    const int64_t j = nb[n];
+    const A sig = bwd ? sg : -sg;
+    const A scl = (P == 2) ? (A)isc[j] : A(1);
+    cx<A> *hs = sh + (n & 1) * (2 * D * 32);
+    // 1. project this warp's colours of psi(j)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = a0 + r;
+      if (c < D) {
+        cx<A> psi[4], h0, h1;
+        ld_colour<P>(in, Vh, j, c, psi);
+        switch (mu) {
+          case 0: project<0>(sig, psi, h0, h1); break;
+          case 1: project<1>(sig, psi, h0, h1); break;
+          case 2: project<2>(sig, psi, h0, h1); break;
+          default: project<3>(sig, psi, h0, h1); break;
+        }
+        if (P == 2) {
+          h0 = scale(scl, h0);
+          h1 = scale(scl, h1);
+        }
+        hs[(2 * c) * 32 + lane] = h0;
+        hs[(2 * c + 1) * 32 + lane] = h1;
+      }
+    }
+    __syncthreads();
+    // 2. this warp's rows of U h (forward) or U^+ h (backward)
+    const void *lk = reinterpret_cast<const char *>(k.links) +
+                     (size_t)(((bwd ? 1 - p : p) * 4 + mu) * slab) * es;
+    cx<A> r0[R], r1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) r0[r] = r1[r] = mk(A(0), A(0));
+    if (bwd) rows_mul<D, REAL, P, R, true>(hs, lane, a0, lk, j, Vh, r0, r1);
+    else rows_mul<D, REAL, P, R, false>(hs, lane, a0, lk, ii, Vh, r0, r1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (a0 + r < D) {
+        switch (mu) {
+          case 0: reconstruct<0>(sig, r0[r], r1[r], acc[r]); break;
+          case 1: reconstruct<1>(sig, r0[r], r1[r], acc[r]); break;
+          case 2: reconstruct<2>(sig, r0[r], r1[r], acc[r]); break;
+          default: reconstruct<3>(sig, r0[r], r1[r], acc[r]); break;
+        }
+      }
+    }
+  }
+
+  // ---- epilogue (no clover) ----
+  const A coef = (A)k.coef;
+  const void *self = (k.mode == HOP_SELF) ? reinterpret_cast<const char *>(k.self) + roff : nullptr;
+  const A ssc = (P == 2 && self) ? (A)f16_scales(self, Vh, D)[ii] : A(1);
+  const A dg = (A)k.diag;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int c = a0 + r;
+    if (c < D) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = scale(coef, acc[r][q]);
+      if (self) {
+        cx<A> sv[4];
+        ld_colour<P>(self, Vh, ii, c, sv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = axpy_r(dg * ssc, sv[q], acc[r][q]);
+      }
+    }
+  }
+  if (P == 2) {
+    // per-site maximum over all D colours: this warp's rows, then across warps
+    float *red = reinterpret_cast<float *>(smem + (size_t)2 * 2 * D * 32 * sizeof(cx<A>));
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (a0 + r < D)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m = fmaxf(m, fmaxf(fabsf((float)acc[r][q].x), fabsf((float)acc[r][q].y)));
+    red[w * 32 + lane] = m;
+    __syncthreads();
+    m = 0.f;
+#pragma unroll
+    for (int v = 0; v < W; ++v) m = fmaxf(m, red[v * 32 + lane]);
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = a0 + r;
+        if (c < D) {
+          cx<float> v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = mk((float)acc[r][q].x * inv, (float)acc[r][q].y * inv);
+          st_colour16(out, Vh, i, c, v);
+        }
+      }
+      if (w == 0) f16_scales_w(out, Vh, D)[i] = m;
+    }
+  } else if (active) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int c = a0 + r;
+      if (c < D) {
+        if (P == 0) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[r]));
+        else st_colour32(out, Vh, i, c, reinterpret_cast<const cx<float> *>(acc[r]));
+      }
+    }
+  }
+}
+
+template <int D, bool REAL, int P, int R>
+__global__ void __launch_bounds__(RowsGeom<D, R>::NT) hop_rows_kernel(HopK k) {
+  extern __shared__ __align__(16) unsigned char rows_smem[];
+  int64_t tile;
+  int rhs;
+  block_tile(k, tile, rhs);
+  hop_rows_tile<D, REAL, P, R>(k, tile, rhs, rows_smem);
+}
+
+// Persistent multi-lattice form (work list of (lattice, tile of 32 sites)).
+// Between items no extra barrier is needed: an item writes buffer 0 first,
+// last read at the previous item's neighbour 6, and every warp has passed
+// that item's neighbour-7 barrier; the FP16 reduction array is rewritten only
+// after 8 more barriers, by which time every warp has read it.
+template <int D, bool REAL, int P, int R>
+__global__ void __launch_bounds__(RowsGeom<D, R>::NT) hop_rows_multi_kernel(const HopK *descs, const int2 *items,
+                                                                            int nitems, const int *frozen) {
+  extern __shared__ __align__(16) unsigned char rows_smem[];
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int2 it = items[w];
+    if (frozen && frozen[it.x]) continue;
+    const HopK k = descs[it.x];
+    hop_rows_tile<D, REAL, P, R>(k, it.y, 0, rows_smem);
+  }
+}
+
+// Opt the instantiation into its dynamic shared memory (above 48 KB for FP64
+// at large d_R) once per process.
+template <typename F>
+static int rows_smem_optin(F *fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return HR_OK;
+  HR_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return HR_OK;
+}
+
+template <int D, bool REAL, int P, int R>
+int launch_rows(const HopK &k, int nrhs, cudaStream_t st) {
+  constexpr size_t sm = rows_smem_bytes<D, R, P>();
+  static int opt = rows_smem_optin(hop_rows_kernel<D, REAL, P, R>, sm);
+  if (opt != HR_OK) return opt;
+  dim3 grid((unsigned)(((k.Vh + 31) / 32) * nrhs));
+  hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, R>::NT, sm, st>>>(k);
+  return hr_check_launch("hop_rows_kernel");
+}
+
+template <int P>
+int rows_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int rows) {
+  if (a.clover) return HR_ERR_UNSUPPORTED;
+  const HopK k = make_hopk(lat, a);
+  const int d = lat->d;
+  const bool real = lat->is_real != 0;
+#define HR_ROWS_CASE(DD, RE, RR) \
+  if (d == DD && real == RE && rows == RR) return launch_rows<DD, RE, P, RR>(k, a.nrhs, s);
+  HR_ROWS_SHAPES(HR_ROWS_CASE)
+#undef HR_ROWS_CASE
+  return HR_ERR_UNSUPPORTED;
+}
+
+template <int P>
+static const void *rows_multi_ptr(int d, int is_real, int rows, int *block, size_t *smem) {
+  const bool real = is_real != 0;
+#define HR_ROWS_CASE(DD, RE, RR)                                                  \
+  if (d == DD && real == RE && rows == RR) {                                      \
+    *block = RowsGeom<DD, RR>::NT;                                                \
+    *smem = rows_smem_bytes<DD, RR, P>();                                         \
+    static int opt = rows_smem_optin(hop_rows_multi_kernel<DD, RE, P, RR>, *smem); \
+    return opt == HR_OK ? (const void *)hop_rows_multi_kernel<DD, RE, P, RR> : nullptr; \
+  }
+  HR_ROWS_SHAPES(HR_ROWS_CASE)
+#undef HR_ROWS_CASE
+  return nullptr;
+}

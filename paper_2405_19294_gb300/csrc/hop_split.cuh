@@ -20,6 +20,7 @@
 #pragma once
 
 #include "hop.cuh"
+#include "hop_rows.cuh"
 
 // One tile of 128/G output sites of right-hand side rhs; `sh` is the block's
 // double-buffered half-spinor staging area.  Every lane of the block must
@@ -247,6 +248,8 @@ static const void *multi_kernel_ptr(int d, int is_real, HopShape sh, int *block)
       if (d == 4) return (const void *)hop_multi_kernel<4, false, P>;
       if (d == 5) return (const void *)hop_multi_kernel<5, false, P>;
       if (d == 6) return (const void *)hop_multi_kernel<6, false, P>;
+      if (d == 7) return (const void *)hop_multi_kernel<7, false, P>;
+      if (d == 8) return (const void *)hop_multi_kernel<8, false, P>;
     }
     return nullptr;
   }
@@ -277,17 +280,19 @@ template <int P>
 int hop_multi_launch(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
                      const int *frozen, cudaStream_t s) {
   int block = 0;
-  const void *fn = multi_kernel_ptr<P>(d, is_real, sh, &block);
+  size_t smem = 0;
+  const void *fn = sh.rows ? rows_multi_ptr<P>(d, is_real, sh.rows, &block, &smem)
+                           : multi_kernel_ptr<P>(d, is_real, sh, &block);
   if (!fn) return HR_ERR_UNSUPPORTED;
   if (nitems <= 0) return HR_OK;
   int dev = 0, sms = 0, per_sm = 0;
   HR_CUDA(cudaGetDevice(&dev));
   HR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
+  HR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > nitems) grid = nitems;
   void *args[] = {(void *)&descs, (void *)&items, (void *)&nitems, (void *)&frozen};
-  HR_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s));
+  HR_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
   return HR_OK;
 }

@@ -135,13 +135,38 @@ struct HopArgs {
 // G threads per site (128 threads per block).
 // mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
 // links staged once per site for all right-hand sides of the block).
+// rows = R > 0 selects the rows kernel: R output colour rows per warp,
+// ceil(d/R) warps per block, 32 sites per block on the lanes.
 struct HopShape {
   int split_g;
   int bs;
   int regs;
   int mrhs;
+  int rows;
 };
-#define HR_MAX_SHAPES 16
+// Integer form of a shape (hr_tuned_shape and friends):
+// rows * 1e8 + mrhs * 1e6 + regs * 1e5 + split_g * 1e3 + bs.
+static inline int hr_shape_code(const HopShape &s) {
+  return s.rows * 100000000 + s.mrhs * 1000000 + s.regs * 100000 + s.split_g * 1000 + s.bs;
+}
+// sites covered by one block (one work-list tile) of a shape
+static inline int hr_shape_tile(const HopShape &s) {
+  return s.rows ? 32 : (s.split_g ? 128 / s.split_g : s.bs);
+}
+#define HR_MAX_SHAPES 24
+
+// largest N of SU(N) (fundamental representation; the 2-index ones stop at 6)
+#define HR_MAX_NC 12
+
+// The (d_R, rows per warp) pairs built for the rows kernel; one X(D, REAL, R)
+// line each.  Shared by the candidate list and every dispatch.
+#define HR_ROWS_SHAPES(X)                                                                               \
+  X(6, false, 2) X(6, false, 3) X(7, false, 2) X(7, false, 4) X(8, false, 2) X(8, false, 4)             \
+  X(8, true, 2) X(8, true, 4) X(9, false, 2) X(9, false, 3) X(10, false, 2) X(10, false, 5)             \
+  X(11, false, 3) X(11, false, 4) X(12, false, 3) X(12, false, 4) X(15, false, 3) X(15, false, 5)       \
+  X(15, true, 3) X(15, true, 5) X(21, false, 3) X(21, false, 4) X(24, true, 3) X(24, true, 4)           \
+  X(35, true, 4) X(35, true, 5)
+
 
 // Candidate shapes for (d, real, precision, several rhs); clover restricts to
 // split_g = 0.

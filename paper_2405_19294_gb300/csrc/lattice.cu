@@ -51,7 +51,8 @@ extern "C" int hr_lattice_create(int T, int L, int N, int rep, hr_lattice **out)
   if (!out) return HR_ERR_ARG;
   *out = nullptr;
   if (T < 2 || L < 2 || (T & 1) || (L & 1)) return HR_ERR_ARG;
-  if (N < 2 || N > 6 || rep < HR_FUND || rep > HR_ASYM) return HR_ERR_ARG;
+  if (N < 2 || N > HR_MAX_NC || rep < HR_FUND || rep > HR_ASYM) return HR_ERR_ARG;
+  if (N > 6 && rep != HR_FUND) return HR_ERR_ARG;
   if (N == 2 && rep == HR_ASYM) return HR_ERR_ARG;
   const int64_t V = (int64_t)T * L * L * L;
   if (V > ((int64_t)1 << 30)) return HR_ERR_ARG;

@@ -20,8 +20,9 @@
 
 int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopShape *out) {
   int n = 0;
-  const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
-  if (site && multi_rhs) {
+  const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 8);
+  const bool site_mrhs = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
+  if (site_mrhs && multi_rhs) {
     // links staged once per site for all right-hand sides of a block
     out[n++] = HopShape{0, 0, 0, 16};
     out[n++] = HopShape{0, 0, 0, 8};
@@ -40,6 +41,11 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
     }
   }
   if (!clover) {
+    // rows kernel: every (d_R, R) pair built in hop_rows.cuh
+#define HR_ROWS_CAND(DD, RE, RR) \
+  if (d == DD && (is_real != 0) == RE) out[n++] = HopShape{0, 32 * ((DD + RR - 1) / RR), 0, 0, RR};
+    HR_ROWS_SHAPES(HR_ROWS_CAND)
+#undef HR_ROWS_CAND
     int gs[2] = {0, 0};
     if (is_real) {
       if (d == 8) { gs[0] = 2; gs[1] = 4; }
@@ -124,7 +130,7 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 }
 
 // Report the tuned shape for the lattice's hop at (prec, nrhs, clover): returns
-// mrhs * 10000000 + regs * 1000000 + split_g * 1000 + block size, or -1 if not tuned yet.
+// its hr_shape_code, or -1 if not tuned yet.
 extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover) {
   if (!lat) return -1;
   HopArgs a;
@@ -134,7 +140,7 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_best.find(tune_key(lat, prec, a));
   if (it == g_best.end()) return -1;
-  return it->second.mrhs * 10000000 + it->second.regs * 1000000 + it->second.split_g * 1000 + it->second.bs;
+  return hr_shape_code(it->second);
 }
 
 // Candidate shapes of this lattice's hop, encoded as hr_tuned_shape reports them.
@@ -143,7 +149,7 @@ extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n && k < max; ++k)
-    out[k] = shapes[k].mrhs * 10000000 + shapes[k].regs * 1000000 + shapes[k].split_g * 1000 + shapes[k].bs;
+    out[k] = hr_shape_code(shapes[k]);
   return n;
 }
 
@@ -154,7 +160,7 @@ extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int
   HopShape shapes[HR_MAX_SHAPES];
   const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n; ++k)
-    if (shapes[k].mrhs * 10000000 + shapes[k].regs * 1000000 + shapes[k].split_g * 1000 + shapes[k].bs == shape) {
+    if (hr_shape_code(shapes[k]) == shape) {
       HopArgs a;
       memset(&a, 0, sizeof(a));
       a.nrhs = nrhs;

@@ -69,6 +69,7 @@ _SIGS = {
     "hr_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
     "hr_batch_destroy": (C.c_int, [_P]),
     "hr_batch_set_stream": (C.c_int, [_P, _P]),
+    "hr_batch_set_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
     "hr_batch_dphi": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int]),
     "hr_batch_cg_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(hr_cg_params), C.POINTER(hr_cg_stats)]),
@@ -194,26 +195,25 @@ class Lattice:
 
     @staticmethod
     def _decode(v):
-        return ((v % 1000000) // 1000, v % 1000, (v % 10000000) // 1000000, v // 10000000)
+        return ((v % 100000) // 1000, v % 1000, (v % 1000000) // 100000, (v % 100000000) // 1000000,
+                v // 100000000)
 
     def tuned_shape(self, prec: int, nrhs: int = 1, clover: bool = False):
-        """(G threads per site or 0, threads per block, register budget, multi-rhs sites per block)
-        chosen by the autotuner, or None."""
+        """(G threads per site or 0, threads per block, register budget, multi-rhs sites per block,
+        rows per warp of the rows kernel or 0) chosen by the autotuner, or None."""
         v = _lib.hr_tuned_shape(self._h, prec, nrhs, int(clover))
         return None if v < 0 else self._decode(v)
 
     def shape_candidates(self, prec: int, nrhs: int = 1, clover: bool = False):
-        buf = (C.c_int * 16)()
-        n = _lib.hr_hop_shape_candidates(self._h, prec, nrhs, int(clover), buf, 16)
+        buf = (C.c_int * 32)()
+        n = _lib.hr_hop_shape_candidates(self._h, prec, nrhs, int(clover), buf, 32)
         if n < 0:
             raise HrError(n, "hr_hop_shape_candidates")
-        return [self._decode(v) for v in buf[:min(n, 16)]]
+        return [self._decode(v) for v in buf[:min(n, 32)]]
 
     def set_shape(self, prec: int, shape, nrhs: int = 1, clover: bool = False):
-        g, bs, regs = shape[0], shape[1], shape[2]
-        mr = shape[3] if len(shape) > 3 else 0
-        code = mr * 10000000 + regs * 1000000 + g * 1000 + bs
-        _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), code), "hr_set_tuned_shape")
+        _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), _shape_code(shape)),
+               "hr_set_tuned_shape")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
         out = (C.c_double * nrhs)()
@@ -231,6 +231,14 @@ class Lattice:
         return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
                 "true_residual": st.true_residual, "seconds": st.seconds,
                 "hop_launches": st.hop_launches}
+
+
+def _shape_code(shape):
+    """(G, block, regs[, mrhs[, rows]]) -> the integer code of the C ABI."""
+    g, bs, regs = shape[0], shape[1], shape[2]
+    mr = shape[3] if len(shape) > 3 else 0
+    rows = shape[4] if len(shape) > 4 else 0
+    return rows * 100000000 + mr * 1000000 + regs * 100000 + g * 1000 + bs
 
 
 class Batch:
@@ -259,6 +267,10 @@ class Batch:
 
     def _ptrs(self, ts):
         return (_P * len(ts))(*[_ptr(t) for t in ts])
+
+    def set_shape(self, d: int, is_real: bool, prec: int, shape):
+        """Pin the launch shape (a tuple as Lattice.shape_candidates lists them) of class (d, is_real)."""
+        _check(_lib.hr_batch_set_shape(self._h, d, int(is_real), prec, _shape_code(shape)), "hr_batch_set_shape")
 
     def dphi(self, outs, ins, parity: int, m0s, prec: int, dagger: bool = False):
         m = (C.c_double * len(m0s))(*m0s)

@@ -45,5 +45,5 @@ def test_create_rejects_bad_shapes_before_touching_the_device():
     from paper_2405_19294_gb300 import build
     lib = ctypes.CDLL(build.build())
     h = ctypes.c_void_p()
-    for args in [(3, 4, 3, 0), (4, 3, 3, 0), (4, 4, 1, 0), (4, 4, 7, 0), (4, 4, 2, 3), (4, 4, 3, 9)]:
+    for args in [(3, 4, 3, 0), (4, 3, 3, 0), (4, 4, 1, 0), (4, 4, 13, 0), (4, 4, 7, 1), (4, 4, 2, 3), (4, 4, 3, 9)]:
         assert lib.hr_lattice_create(*args, ctypes.byref(h)) == -1

@@ -123,3 +123,36 @@ def test_batch_64_lattices_to_1e8(hr):
         res = np.linalg.norm(be[sites] - Mx[sites]) / np.linalg.norm(be[sites])
         assert res < 1e-7, (k, res)
     batch.close()
+
+
+# one lattice per large-d_R class: complex 10, 12, 15, 21 and real 15, 24, 35
+LARGE_BATCH = [(4, 4, 4, "sym"), (4, 2, 12, "fund"), (4, 4, 6, "asym"), (4, 2, 6, "sym"), (4, 4, 4, "adj"),
+               (4, 2, 5, "adj"), (4, 2, 6, "adj")]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batch_every_class_shape(hr, prec):
+    """Each candidate shape of each class, pinned in turn, in the persistent multi-lattice launch."""
+    eps, m0 = 0.5, -0.3
+    lats, ops, psis, ins, outs = [], [], [], [], []
+    for k, (T, L, N, rep) in enumerate(LARGE_BATCH):
+        lat, _ = gpu_lattice(hr, T, L, N, rep, eps, 0.0, seed=20 + k)
+        ops.append(oracle_operator(T, L, N, rep, eps, m0, 0.0, seed=20 + k))
+        psi = inputs.gaussian_spinor(30 + k, T, L, lat.d)[0]
+        lats.append(lat)
+        psis.append(psi)
+        ins.append(_fields(lat, psi, prec))
+        outs.append(lat.new_field(0, prec))
+    batch = hr.Batch(lats)
+    refs = [ops[k].apply_schur(psis[k], 0) for k in range(len(lats))]
+    nshape = max(len(l.shape_candidates(prec)) for l in lats)
+    for s in range(nshape):
+        for lat in lats:
+            cands = lat.shape_candidates(prec)
+            batch.set_shape(lat.d, lat.is_real, prec, cands[min(s, len(cands) - 1)])
+        batch.dphi(outs, ins, 0, [m0] * len(lats), prec, False)
+        torch.cuda.synchronize()
+        for k, lat in enumerate(lats):
+            got = _unpack(lat, outs[k], prec)
+            assert rel_err(got, refs[k], ops[k].geom.parity == 0) < TOL[prec], (s, LARGE_BATCH[k])
+    batch.close()

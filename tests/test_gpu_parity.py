@@ -182,7 +182,7 @@ def test_errors_are_reported(hr):
     with pytest.raises(hr.HrError):
         hr.Lattice(4, 4, 2, "asym")        # trivial singlet
     with pytest.raises(hr.HrError):
-        hr.Lattice(4, 4, 7, "fund")        # N out of range
+        hr.Lattice(4, 4, 13, "fund")       # N out of range
     lat = hr.Lattice(4, 4, 3, "fund")
     f = lat.new_field(0, 1)
     with pytest.raises(hr.HrError):
@@ -213,7 +213,7 @@ def test_dphi_parity_large_representations(hr, N, rep, prec):
             assert err < TOL[prec], (parity, dagger, err)
 
 
-@pytest.mark.parametrize("N,rep", [(3, "fund"), (3, "adj"), (3, "sym"), (4, "sym"), (6, "asym"), (5, "adj"),
+@pytest.mark.parametrize("N,rep", [(3, "fund"), (3, "adj"), (3, "sym"), (4, "sym"), (6, "asym"), (5, "adj"), (4, "adj"),
                                    (6, "sym"), (6, "adj")])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_every_tuner_shape_is_correct(hr, N, rep, prec):

@@ -13,6 +13,7 @@ from oracle import sun
 from paper_2405_19294_gb300 import inputs
 
 NS = [2, 3, 4, 5, 6]
+NS_FUND = NS + [7, 8, 10, 12]   # fundamental-only large-N_c workload
 REPS = ["fund", "adj", "sym", "asym"]
 
 
@@ -25,7 +26,7 @@ def _valid(N, rep):
     return not (N == 2 and rep == "asym")
 
 
-@pytest.mark.parametrize("N", NS)
+@pytest.mark.parametrize("N", NS_FUND)
 def test_generators_normalisation_and_completeness(N):
     T = sun.generators(N)
     assert T.shape == (N * N - 1, N, N)
@@ -76,7 +77,7 @@ def test_su2_link_closed_form():
     assert np.max(np.abs(U - ref)) < 1e-14
 
 
-@pytest.mark.parametrize("N", NS)
+@pytest.mark.parametrize("N", NS_FUND)
 def test_links_match_pade_expm_and_are_special_unitary(N):
     a = inputs.algebra_coefficients(7, 2, 2, N).reshape(-1, N * N - 1)[:40]
     eps = 1.0
@@ -89,7 +90,7 @@ def test_links_match_pade_expm_and_are_special_unitary(N):
     assert np.allclose(np.linalg.det(U), 1.0, atol=1e-13)
 
 
-@pytest.mark.parametrize("N", NS)
+@pytest.mark.parametrize("N", NS_FUND)
 def test_reunitarise_matches_qr_and_fixes_det(N):
     rng = np.random.default_rng(3)
     M = rng.standard_normal((30, N, N)) + 1j * rng.standard_normal((30, N, N))
@@ -109,7 +110,7 @@ def test_reunitarise_matches_qr_and_fixes_det(N):
         assert np.allclose(ratio, ratio[0], atol=1e-12)
 
 
-@pytest.mark.parametrize("N", NS)
+@pytest.mark.parametrize("N", NS_FUND)
 def test_reunitarise_is_identity_on_sun(N):
     U = sun.links_from_algebra(np.random.default_rng(5).standard_normal((20, N * N - 1)), 1.0, N)
     assert np.max(np.abs(sun.reunitarise(U) - U)) < 1e-13
