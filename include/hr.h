@@ -305,6 +305,51 @@ int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, in
 int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
                       const hr_cg_params *params, hr_cg_stats *stats);
 
+/* ---- time-slab domain decomposition (Sec. 2, halo-ready geometry) -------- */
+
+/* A sub-domain: the time slab [t0, t0 + T_loc) of a T_global x L^3 lattice,
+ * with the same N and rep.  T_loc >= 2, t0 and T_global even, t0 + T_loc <=
+ * T_global.  Load its links with hr_represent_links from the canonical FP64
+ * links of its own sites U[V_loc][4][N][N] (lexicographic in local
+ * coordinates, local t = global t - t0); the antiperiodic sign is applied at
+ * global t = T_global - 1.  Only csw = 0 (the clover leaves would need a link
+ * halo: HR_ERR_UNSUPPORTED); hr_dphi and the solvers treat the slab as
+ * periodic on its own, the calls below couple the slabs.  Errors: HR_ERR_ARG. */
+int hr_lattice_create_domain(int T_loc, int L, int N, int rep, int t0, int T_global, hr_lattice **out);
+
+/* Bytes of one face buffer for nrhs right-hand sides: [rhs][2][d][L^3/2]
+ * complex, FP64 for prec HR_F64 and FP32 otherwise. */
+int hr_domain_halo_bytes(const hr_lattice *lat, int prec, int nrhs, size_t *bytes);
+
+/* One of the two hops of Dhat_p on a slab, first half (Sec. 2: send-buffer
+ * synchronisation with half-spinors, masked directions):
+ *   stage 0: out = tmp_q = -1/(2(4+m0)) H in_hop, out_parity = q = 1-p;
+ *   stage 1: out = out_p = (4+m0) self + 1/2 H in_hop, out_parity = p,
+ *            in_hop = tmp_q, self = the Dhat input (parity p).
+ * Writes the send buffers from in_hop's boundary sites -- send_down: the
+ * projected half-spinors of the bottom face (local t = 0) for the slab below;
+ * send_up: U_0^+ times the projected half-spinors of the top face for the
+ * slab above -- and runs the bulk hop with the two t hops that cross a face
+ * masked.  Fields: internal, precision prec, nrhs consecutive rhs; buffers:
+ * device memory of hr_domain_halo_bytes, caller-owned.  Asynchronous on the
+ * lattice's stream.  Errors: HR_ERR_ARG, HR_ERR_STATE (not a slab, links
+ * missing), HR_ERR_UNSUPPORTED (clover). */
+int hr_domain_hop_begin(hr_lattice *lat, void *out, const void *in_hop, const void *self, int out_parity,
+                        double m0, int prec, int nrhs, int dagger, int stage, void *send_up, void *send_down);
+
+/* Second half, after the exchange: recv_up holds the send_down buffer of the
+ * slab above, recv_down the send_up buffer of the slab below (periodically:
+ * with one slab, its own).  Adds the masked face terms to out. */
+int hr_domain_hop_end(hr_lattice *lat, void *out, int out_parity, double m0, int prec, int nrhs, int dagger,
+                      int stage, const void *recv_up, const void *recv_down);
+
+/* All n slabs of one lattice in this process (lats in time order, covering
+ * [0, T_global)): out[k] = Dhat_p in[k] on slab k, the exchange done as
+ * device-to-device copies between the slabs' own buffers, everything on the
+ * first slab's stream.  Errors as above. */
+int hr_domains_dphi(int n, hr_lattice *const *lats, void *const *out, const void *const *in, int parity, double m0,
+                    int prec, int nrhs, int dagger);
+
 /* Human-readable text of an hr_status. */
 const char *hr_status_string(int status);
 

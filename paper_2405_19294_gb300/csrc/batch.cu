@@ -156,7 +156,9 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
   for (int i = 0; i < n; ++i) {
     if (!lats[i]) return HR_ERR_ARG;
     if (!lats[i]->have_links) return HR_ERR_STATE;
-    if (lats[i]->csw != 0.0) return HR_ERR_UNSUPPORTED;
+    if (lats[i]->csw != 0.0 || lats[i]->dom) return HR_ERR_UNSUPPORTED;
+    // the rows kernel reads the rows link layout, built with the links when csw = 0
+    if (hr_has_rows_shapes(lats[i]->d, lats[i]->is_real) && !lats[i]->rlinks[HR_F16]) return HR_ERR_STATE;
   }
   hr_batch *b = new hr_batch();
   b->n = n;
@@ -278,6 +280,7 @@ static int fill_desc(hr_batch *b, int slot0, int prec, void *const *out, const v
     HopArgs a;
     memset(&a, 0, sizeof(a));
     a.links = lat->links[prec];
+    a.rlinks = lat->rlinks[prec];
     a.dagger = dagger;
     a.nrhs = 1;
     a.field_stride = fb;

@@ -54,9 +54,9 @@ __device__ __forceinline__ cx<R> scale(R s, cx<R> a) { return mk(s * a.x, s * a.
 // ------------------------------------------------------------ precisions ----
 // P = 0 (FP64), 1 (FP32), 2 (FP16); A = accumulation type.
 template <int P> struct PT;
-template <> struct PT<0> { typedef double A; };
-template <> struct PT<1> { typedef float A; };
-template <> struct PT<2> { typedef float A; };
+template <> struct PT<0> { typedef double A; typedef double2 S2; };   // S2: one stored 2-real chunk
+template <> struct PT<1> { typedef float A; typedef float2 S2; };
+template <> struct PT<2> { typedef float A; typedef __half2 S2; };
 
 // 2-real chunk k (link or clover) of site i, converted to the accumulation type
 template <int P>

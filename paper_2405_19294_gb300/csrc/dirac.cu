@@ -436,6 +436,7 @@ int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double 
   HopArgs a;
   memset(&a, 0, sizeof(a));
   a.links = lat->links[prec];
+  a.rlinks = lat->rlinks[prec];
   a.dagger = dagger;
   a.nrhs = nrhs;
   if (parity == HR_FULL) {

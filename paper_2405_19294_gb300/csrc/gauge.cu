@@ -213,7 +213,7 @@ extern "C" int hr_links_from_algebra(hr_lattice *lat, double *U_dev, const doubl
 
 // ----------------------------------------------------------- U -> U_R ------
 struct RepK {
-  int T, L, Lh, N, rep, d, nch, reun;
+  int T, L, Lh, N, rep, d, nch, reun, t0, Tg;
   int64_t V, Vh;
 };
 
@@ -262,7 +262,7 @@ __global__ void represent_kernel(void *l64, void *l32, void *l16, const double *
   const int tt = (int)(x / ((int64_t)k.L * k.L * k.L));
   const int par = (tt + xx + yy + zz) & 1;
   const int64_t i = cb_index(tt, xx, yy, zz, k.L, k.Lh);
-  const double sg = (mu == 0 && tt == k.T - 1) ? -1.0 : 1.0;  // antiperiodic time
+  const double sg = (mu == 0 && k.t0 + tt == k.Tg - 1) ? -1.0 : 1.0;  // antiperiodic in global time
   const int64_t base = ((int64_t)(par * 4 + mu) * k.nch) * k.Vh;
   if (k.rep == HR_ADJ) {
     for (int q = 0; q < k.nch; ++q) {
@@ -289,8 +289,92 @@ __global__ void represent_kernel(void *l64, void *l32, void *l16, const double *
 
 int hr_clover_build(hr_lattice *lat);
 
+// ------------------------------------------------ rows-kernel link layout ----
+// One thread per (output parity p, direction n, output site i): V_n(x) from
+// the FP64 internal links -- U_R,mu(x) itself (n even) or the adjoint of
+// U_R,mu(x - mu) (n odd, read from the other parity's slot) -- written
+// row-major at the output site in all three precisions (hr_rows_nch).
+__global__ void rows_links_kernel(void *r64, void *r32, void *r16, const void *l64, RepK k) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 16 * k.Vh) return;
+  const int64_t i = g % k.Vh;
+  const int pn = (int)(g / k.Vh);  // p * 8 + n
+  const int p = pn >> 3, n = pn & 7, mu = n >> 1;
+  const bool back = n & 1;
+  const int d = k.d;
+  const bool real = k.rep == HR_ADJ;
+  const Site s = site_of(i, p, k.L, k.Lh);
+  int c4[4] = {s.t, s.x, s.y, s.z};
+  const int ext[4] = {k.T, k.L, k.L, k.L};
+  int64_t j = i;
+  int sp = p;
+  if (back) {
+    c4[mu] = (c4[mu] + ext[mu] - 1) % ext[mu];
+    j = cb_index(c4[0], c4[1], c4[2], c4[3], k.L, k.Lh);
+    sp = 1 - p;
+  }
+  const double2 *src = reinterpret_cast<const double2 *>(l64) + ((int64_t)(sp * 4 + mu) * k.nch) * k.Vh;
+  const int dp = hr_rows_dp(d, real), nch = hr_rows_nch(d, real);
+  const int64_t obase = (int64_t)pn * nch * k.Vh + i;
+  double2 *o64 = reinterpret_cast<double2 *>(r64);
+  float2 *o32 = reinterpret_cast<float2 *>(r32);
+  __half2 *o16 = reinterpret_cast<__half2 *>(r16);
+  // U element (a, c) at the source site
+  auto uel = [&](int a, int c) -> zd {
+    const int e = a * d + c;
+    if (real) {
+      const double2 v = src[(int64_t)(e >> 1) * k.Vh + j];
+      return mk((e & 1) ? v.y : v.x, 0.0);
+    }
+    const double2 v = src[(int64_t)e * k.Vh + j];
+    return mk(v.x, v.y);
+  };
+  auto vel = [&](int a, int c) -> zd {  // V[a][c]
+    if (c >= d) return mk(0.0, 0.0);
+    return back ? zconj(uel(c, a)) : uel(a, c);
+  };
+  if (real) {
+    for (int a = 0; a < d; ++a)
+      for (int c = 0; c < dp; c += 2) {
+        const double v0 = vel(a, c).x, v1 = vel(a, c + 1).x;
+        const int64_t idx = obase + (int64_t)((a * dp + c) >> 1) * k.Vh;
+        o64[idx] = make_double2(v0, v1);
+        o32[idx] = make_float2((float)v0, (float)v1);
+        o16[idx] = __floats2half2_rn((float)v0, (float)v1);
+      }
+  } else {
+    for (int a = 0; a < d; ++a)
+      for (int c = 0; c < d; ++c) {
+        const zd v = vel(a, c);
+        const int64_t idx = obase + (int64_t)(a * d + c) * k.Vh;
+        o64[idx] = make_double2(v.x, v.y);
+        o32[idx] = make_float2((float)v.x, (float)v.y);
+        o16[idx] = __floats2half2_rn((float)v.x, (float)v.y);
+      }
+  }
+}
+
+// 16 matrices of hr_rows_nch chunk rows, then HR_ROWS_SLACK zeroed chunk rows
+// that the rows kernel's last column batch may read past the last matrix.
+#define HR_ROWS_SLACK 16
+static int hr_rows_links_build(hr_lattice *lat, const RepK &k) {
+  const size_t nrows = (size_t)16 * hr_rows_nch(lat->d, lat->is_real);
+  const size_t es[3] = {16, 8, 4};
+  for (int p = 0; p < 3; ++p) {
+    if (!lat->rlinks[p])
+      HR_CUDA(cudaMalloc(&lat->rlinks[p], (nrows + HR_ROWS_SLACK) * (size_t)lat->Vh * es[p]));
+    HR_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(lat->rlinks[p]) + nrows * (size_t)lat->Vh * es[p], 0,
+                            (size_t)HR_ROWS_SLACK * lat->Vh * es[p], lat->stream));
+  }
+  const int64_t nt = 16 * lat->Vh;
+  rows_links_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, lat->stream>>>(lat->rlinks[0], lat->rlinks[1],
+                                                                          lat->rlinks[2], lat->links[0], k);
+  return hr_check_launch("rows_links_kernel");
+}
+
 extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reunitarise, double csw) {
   if (!lat || !U_dev) return HR_ERR_ARG;
+  if (lat->dom && csw != 0.0) return HR_ERR_UNSUPPORTED;  // the clover leaves would need a link halo
   const size_t nchunks = (size_t)2 * 4 * lat->nch_link * (size_t)lat->Vh;
   const size_t es[3] = {16, 8, 4};
   for (int p = 0; p < 3; ++p)
@@ -306,6 +390,8 @@ extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reun
   k.reun = reunitarise;
   k.V = lat->V;
   k.Vh = lat->Vh;
+  k.t0 = lat->t0;
+  k.Tg = lat->Tg;
   const int64_t nl = lat->V * 4;
   if (lat->N <= 6)
     represent_kernel<6><<<(unsigned)((nl + 63) / 64), 64, 0, lat->stream>>>(lat->links[0], lat->links[1],
@@ -314,6 +400,8 @@ extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reun
     represent_kernel<HR_MAX_NC><<<(unsigned)((nl + 63) / 64), 64, 0, lat->stream>>>(lat->links[0], lat->links[1],
                                                                                   lat->links[2], U_dev, k);
   HR_TRY(hr_check_launch("represent_kernel"));
+  // the rows kernel (no clover) reads its own layout of the same links
+  if (csw == 0.0 && !lat->dom && hr_has_rows_shapes(lat->d, lat->is_real)) HR_TRY(hr_rows_links_build(lat, k));
   lat->have_links = 1;
   lat->csw = csw;
   lat->clover_cached = 0;
@@ -364,6 +452,8 @@ extern "C" int hr_export_represented_links(hr_lattice *lat, double *UR_dev) {
   k.reun = 0;
   k.V = lat->V;
   k.Vh = lat->Vh;
+  k.t0 = lat->t0;
+  k.Tg = lat->Tg;
   const int64_t nl = lat->V * 4;
   export_links_kernel<<<(unsigned)((nl + 127) / 128), 128, 0, lat->stream>>>(UR_dev, lat->links[0], k);
   return hr_check_launch("export_links_kernel");

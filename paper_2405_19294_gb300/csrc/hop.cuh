@@ -29,8 +29,9 @@ struct HopK {
   const void *in;
   const void *self;
   const void *links;
+  const void *rlinks;
   const void *clover;
-  int T, L, Lh, p, mode, nch, nrhs;
+  int T, L, Lh, p, mode, nch, nrhs, tmask;
   int64_t Vh;
   size_t stride;
   double sgn, coef, diag;
@@ -208,12 +209,14 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
     for (int q = 0; q < 4; ++q) acc[c][q] = mk(A(0), A(0));
 
   const int64_t LLh = (int64_t)L * Lh;
-  // mu = 0 (t)
+  // mu = 0 (t); on a time slab (tmask) the hops across its faces come later from the halo
   {
     const int tf = (s.t + 1 == T) ? 0 : s.t + 1, tb = (s.t == 0) ? T - 1 : s.t - 1;
     const int64_t jf = i + (int64_t)(tf - s.t) * L * LLh, jb = i + (int64_t)(tb - s.t) * L * LLh;
-    hop_dir<D, REAL, P, 0, false>(acc, in, Vh, jf, slot(p, 0), i, -sg, P == 2 ? (A)isc[jf] : A(1));
-    hop_dir<D, REAL, P, 0, true>(acc, in, Vh, jb, slot(1 - p, 0), jb, sg, P == 2 ? (A)isc[jb] : A(1));
+    if (!(k.tmask && s.t == T - 1))
+      hop_dir<D, REAL, P, 0, false>(acc, in, Vh, jf, slot(p, 0), i, -sg, P == 2 ? (A)isc[jf] : A(1));
+    if (!(k.tmask && s.t == 0))
+      hop_dir<D, REAL, P, 0, true>(acc, in, Vh, jb, slot(1 - p, 0), jb, sg, P == 2 ? (A)isc[jb] : A(1));
   }
   // mu = 1 (x)
   {
@@ -328,6 +331,7 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   k.in = a.in;
   k.self = a.self;
   k.links = a.links;
+  k.rlinks = a.rlinks;
   k.clover = a.clover;
   k.T = lat->T;
   k.L = lat->L;
@@ -341,6 +345,7 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   k.coef = a.coef;
   k.diag = a.diag;
   k.nrhs = a.nrhs;
+  k.tmask = a.tmask;
   return k;
 }
 

@@ -14,24 +14,11 @@ int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, H
   if (a.clover) return HR_ERR_UNSUPPORTED;
   const HopK k = make_hopk(lat, a);
   const int g = sh.split_g;
-  if (lat->is_real) {
-    if (d == 8 && g == 2) return launch_split<8, true, 2, 2>(k, a.nrhs, s);
-    if (d == 8 && g == 4) return launch_split<8, true, 2, 4>(k, a.nrhs, s);
-    if (d == 15 && g == 4) return launch_split<15, true, 2, 4>(k, a.nrhs, s);
-    if (d == 15 && g == 8) return launch_split<15, true, 2, 8>(k, a.nrhs, s);
-    if (d == 24 && g == 8) return launch_split<24, true, 2, 8>(k, a.nrhs, s);
-    if (d == 24 && g == 16) return launch_split<24, true, 2, 16>(k, a.nrhs, s);
-    if (d == 35 && g == 8) return launch_split<35, true, 2, 8>(k, a.nrhs, s);
-    if (d == 35 && g == 16) return launch_split<35, true, 2, 16>(k, a.nrhs, s);
-  } else {
-    if (d == 6 && g == 2) return launch_split<6, false, 2, 2>(k, a.nrhs, s);
-    if (d == 10 && g == 2) return launch_split<10, false, 2, 2>(k, a.nrhs, s);
-    if (d == 10 && g == 4) return launch_split<10, false, 2, 4>(k, a.nrhs, s);
-    if (d == 15 && g == 4) return launch_split<15, false, 2, 4>(k, a.nrhs, s);
-    if (d == 15 && g == 8) return launch_split<15, false, 2, 8>(k, a.nrhs, s);
-    if (d == 21 && g == 4) return launch_split<21, false, 2, 4>(k, a.nrhs, s);
-    if (d == 21 && g == 8) return launch_split<21, false, 2, 8>(k, a.nrhs, s);
-  }
+  const bool real = lat->is_real != 0;
+#define HR_SPLIT_CASE(DD, RE, GG) \
+  if (d == DD && real == RE && g == GG) return launch_split<DD, RE, 2, GG>(k, a.nrhs, s);
+  HR_SPLIT_SHAPES(HR_SPLIT_CASE)
+#undef HR_SPLIT_CASE
   return HR_ERR_UNSUPPORTED;
 }
 

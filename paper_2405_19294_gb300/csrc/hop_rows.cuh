@@ -4,70 +4,120 @@
 //
 // Sec. 3.1.2 of the paper parallelises the represented-link product in the
 // representation dimension once a one-site-per-thread kernel runs out of
-// registers.  The colour-split kernel (hop_split.cuh) keeps a site's G threads
-// inside one warp, so one warp-wide link load touches G separate chunk rows of
-// 32/G sites each.  Here every warp instead owns R consecutive output rows
-// a = w R ... w R + R - 1 for the same 32 sites, so every link load of a warp
-// reads one chunk row for 32 consecutive sites (256 B in FP32, fully
-// coalesced).  For each of the 8 neighbours:
+// registers.  Here every warp owns R consecutive output rows a = w R ...
+// w R + R - 1 for the same 32 sites.  The links are read from the rows layout
+// (hr_rows_nch): the 8 matrices an output site needs -- U_R(x) and
+// U_R(x - mu)^+ -- stored at the output site, row-major, so every link load of
+// a warp reads one chunk row of 32 consecutive sites (256 B in FP32, fully
+// coalesced, both halves of a real chunk used).  For each of the 8 neighbours:
 //   1. warp w loads colours c = w R ... of psi(j) for its 32 sites, projects
 //      them (Sec. 2.2) and stores h0[c], h1[c] to shared memory laid out
-//      [colour][lane] (double-buffered per neighbour);
-//   2. one block barrier; then each warp multiplies its R rows of U_R (or
-//      columns of U_R, for U_R^+) with the full half-spinor of its lane's site
-//      (colour outer, rows inner) and rebuilds the 4 spin components.
-// One barrier per neighbour suffices: a warp that writes the buffer of
-// neighbour n+2 has passed the barrier of n+1, which every warp reaches only
-// after it has finished reading neighbour n.  No clover epilogue (the clover
-// term is built for d_R <= 8, where the site kernel is used).
+//      [colour][lane] (double-buffered per neighbour; colours up to a multiple
+//      of the column batch CB, the pad kept at zero);
+//   2. one block barrier; then each warp walks the colours in batches of CB:
+//      it first issues all R x CB link loads of the batch (independent, so
+//      they are in flight together), then multiplies them with the staged
+//      half-spinors, and finally rebuilds the 4 spin components.
+// Rows past d_R (when R does not divide it) are clamped to row d_R - 1: their
+// loads stay in bounds and their results are dropped.  One barrier per
+// neighbour suffices: a warp that writes the buffer of neighbour n+2 has
+// passed the barrier of n+1, which every warp reaches only after it has
+// finished reading neighbour n.  No clover epilogue (the clover term is built
+// for d_R <= 8, where the site kernel is used).
 #pragma once
 
 #include "hop.cuh"
 
-template <int D, int R>
+template <int D, bool REAL, int R>
 struct RowsGeom {
   static constexpr int W = (D + R - 1) / R;  // warps per block
   static constexpr int NT = 32 * W;           // threads per block
+  // colours per load batch: the whole (padded) row for small d_R, else 8-16 loads per batch
+  static constexpr int CB = REAL ? (R * hr_rows_dp(D, true) / 2 <= 24 ? hr_rows_dp(D, true) : (R <= 2 ? 16 : 8))
+                                 : (R * D <= 36 ? D : (R <= 2 ? 8 : 4));
+  static constexpr int DC = (D + CB - 1) / CB * CB;                        // staged colours (padded)
+  static constexpr int DP = hr_rows_dp(D, REAL);
+  static constexpr int NCH = hr_rows_nch(D, REAL);
 };
 
 // bytes of dynamic shared memory: the double-buffered half-spinors plus, for
 // FP16 output, one float per (warp, lane) for the per-site maximum
-template <int D, int R, int P>
+template <int D, bool REAL, int R, int P>
 constexpr size_t rows_smem_bytes() {
-  return (size_t)2 * 2 * D * 32 * sizeof(cx<typename PT<P>::A>) + (P == 2 ? (size_t)RowsGeom<D, R>::W * 32 * 4 : 0);
+  return (size_t)2 * 2 * RowsGeom<D, REAL, R>::DC * 32 * sizeof(cx<typename PT<P>::A>) +
+         (P == 2 ? (size_t)RowsGeom<D, REAL, R>::W * 32 * 4 : 0);
 }
 
-// r0[r] += U[a][c] h0 (or conj(U[c][a]) h0 when ADJ), same for h1, for this
-// warp's rows a = a0 + r < D, all colours c.
-template <int D, bool REAL, int P, int R, bool ADJ>
-__device__ __forceinline__ void rows_mul(const cx<typename PT<P>::A> *hs, int lane, int a0, const void *lk,
-                                         int64_t li, int64_t Vh, cx<typename PT<P>::A> r0[R],
+// r0[r] += V[a_r][c] h0[c], r1[r] += V[a_r][c] h1[c] over all colours, for
+// this warp's rows a_r; `lk` is the chunk-row base of V_n, li the site index.
+template <int D, bool REAL, int P, int R>
+__device__ __forceinline__ void rows_mul(const cx<typename PT<P>::A> *hs, int lane, const int ar[R],
+                                         const void *lk, int64_t li, int64_t Vh, cx<typename PT<P>::A> r0[R],
                                          cx<typename PT<P>::A> r1[R]) {
   typedef typename PT<P>::A A;
-#pragma unroll 3
-  for (int c = 0; c < D; ++c) {
-    const cx<A> h0 = hs[(2 * c) * 32 + lane], h1 = hs[(2 * c + 1) * 32 + lane];
+  typedef RowsGeom<D, REAL, R> G;
+  constexpr int CB = G::CB;
+  // chunk rows of row a_r start at rp[r]; colours past the row (the pad up to
+  // a multiple of CB) read on into the next row or, after the last matrix, into
+  // the zeroed slack of the layout, and meet h = 0
+  constexpr int ROWCH = REAL ? G::DP / 2 : D;
+  const void *rp[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int a = a0 + r;
-      if (a < D) {
-        const int e = ADJ ? (c * D + a) : (a * D + c);
-        if (REAL) {
-          const cx<A> pr = ld2<P>(lk, (int64_t)(e >> 1) * Vh + li);
-          const A ue = (e & 1) ? pr.y : pr.x;
-          r0[r] = rfma(ue, h0, r0[r]);
-          r1[r] = rfma(ue, h1, r1[r]);
-        } else {
-          const cx<A> ue = ld2<P>(lk, (int64_t)e * Vh + li);
-          if (ADJ) {
-            r0[r] = cfmac(ue, h0, r0[r]);
-            r1[r] = cfmac(ue, h1, r1[r]);
-          } else {
-            r0[r] = cfma(ue, h0, r0[r]);
-            r1[r] = cfma(ue, h1, r1[r]);
-          }
+  for (int r = 0; r < R; ++r)
+    rp[r] = reinterpret_cast<const char *>(lk) + (size_t)(ar[r] * ROWCH) * (size_t)Vh * sizeof(typename PT<P>::S2) +
+            (size_t)li * sizeof(typename PT<P>::S2);
+#pragma unroll 1
+  for (int c0 = 0; c0 < G::DC; c0 += CB) {
+    if (REAL) {
+      A u[R][CB];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < CB / 2; ++q) {
+          const cx<A> v = ld2<P>(rp[r], (int64_t)((c0 >> 1) + q) * Vh);
+          u[r][2 * q] = v.x;
+          u[r][2 * q + 1] = v.y;
+        }
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+        const cx<A> h0 = hs[(2 * (c0 + cc)) * 32 + lane], h1 = hs[(2 * (c0 + cc) + 1) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          r0[r] = rfma(u[r][cc], h0, r0[r]);
+          r1[r] = rfma(u[r][cc], h1, r1[r]);
         }
       }
+    } else {
+      cx<A> u[R][CB];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) u[r][cc] = ld2<P>(rp[r], (int64_t)(c0 + cc) * Vh);
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+        const cx<A> h0 = hs[(2 * (c0 + cc)) * 32 + lane], h1 = hs[(2 * (c0 + cc) + 1) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          r0[r] = cfma(u[r][cc], h0, r0[r]);
+          r1[r] = cfma(u[r][cc], h1, r1[r]);
+        }
+      }
+    }
+  }
+}
+
+// Zero the pad colours D ... DC-1 of both half-spinor buffers; called once at
+// kernel start, before the first tile's first barrier.  No tile writes them.
+template <int D, bool REAL, int P, int R>
+__device__ __forceinline__ void rows_zero_pads(unsigned char *smem) {
+  typedef typename PT<P>::A A;
+  typedef RowsGeom<D, REAL, R> G;
+  constexpr int DC = G::DC;
+  if constexpr (DC > D) {
+    cx<A> *sh = reinterpret_cast<cx<A> *>(smem);
+    for (int e = threadIdx.x; e < 2 * 2 * (DC - D) * 32; e += G::NT) {
+      const int buf = e / (2 * (DC - D) * 32), rem = e % (2 * (DC - D) * 32);
+      sh[buf * (2 * DC * 32) + 2 * D * 32 + rem] = mk(A(0), A(0));
     }
   }
 }
@@ -77,8 +127,10 @@ __device__ __forceinline__ void rows_mul(const cx<typename PT<P>::A> *hs, int la
 template <int D, bool REAL, int P, int R>
 __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int rhs, unsigned char *smem) {
   typedef typename PT<P>::A A;
-  constexpr int W = RowsGeom<D, R>::W;
-  cx<A> *sh = reinterpret_cast<cx<A> *>(smem);  // [2][2D][32]
+  typedef RowsGeom<D, REAL, R> G;
+  constexpr int W = G::W;
+  constexpr int DC = G::DC;
+  cx<A> *sh = reinterpret_cast<cx<A> *>(smem);  // [2][2 DC][32]
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int a0 = w * R;
@@ -92,9 +144,12 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
   const int L = k.L, Lh = k.Lh, T = k.T, p = k.p;
   const Site s = site_of(ii, p, L, Lh);
   const A sg = (A)k.sgn;
-  const int64_t slab = (int64_t)k.nch * Vh;
+  const int64_t slab = (int64_t)G::NCH * Vh;  // chunks per [p][n] matrix slot
   const size_t es = (P == 0) ? 16 : (P == 1 ? 8 : 4);
   const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
+  int ar[R];  // this warp's rows, clamped to the last one
+#pragma unroll
+  for (int r = 0; r < R; ++r) ar[r] = (a0 + r < D) ? a0 + r : D - 1;
 
   cx<A> acc[R][4];
 #pragma unroll
@@ -126,7 +181,7 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
     const int64_t j = nb[n];
     const A sig = bwd ? sg : -sg;
     const A scl = (P == 2) ? (A)isc[j] : A(1);
-    cx<A> *hs = sh + (n & 1) * (2 * D * 32);
+    cx<A> *hs = sh + (n & 1) * (2 * DC * 32);
     // 1. project this warp's colours of psi(j)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -149,14 +204,13 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
       }
     }
     __syncthreads();
-    // 2. this warp's rows of U h (forward) or U^+ h (backward)
-    const void *lk = reinterpret_cast<const char *>(k.links) +
-                     (size_t)(((bwd ? 1 - p : p) * 4 + mu) * slab) * es;
+    // 2. this warp's rows of V_n h: V_n = U_R(x) (forward) or U_R(x - mu)^+
+    // (backward), both stored at the output site in the rows layout
+    const void *lk = reinterpret_cast<const char *>(k.rlinks) + (size_t)((p * 8 + n) * slab) * es;
     cx<A> r0[R], r1[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) r0[r] = r1[r] = mk(A(0), A(0));
-    if (bwd) rows_mul<D, REAL, P, R, true>(hs, lane, a0, lk, j, Vh, r0, r1);
-    else rows_mul<D, REAL, P, R, false>(hs, lane, a0, lk, ii, Vh, r0, r1);
+    rows_mul<D, REAL, P, R>(hs, lane, ar, lk, ii, Vh, r0, r1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (a0 + r < D) {
@@ -191,7 +245,7 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
   }
   if (P == 2) {
     // per-site maximum over all D colours: this warp's rows, then across warps
-    float *red = reinterpret_cast<float *>(smem + (size_t)2 * 2 * D * 32 * sizeof(cx<A>));
+    float *red = reinterpret_cast<float *>(smem + (size_t)2 * 2 * DC * 32 * sizeof(cx<A>));
     float m = 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -230,11 +284,12 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
 }
 
 template <int D, bool REAL, int P, int R>
-__global__ void __launch_bounds__(RowsGeom<D, R>::NT) hop_rows_kernel(HopK k) {
+__global__ void __launch_bounds__(RowsGeom<D, REAL, R>::NT) hop_rows_kernel(HopK k) {
   extern __shared__ __align__(16) unsigned char rows_smem[];
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
+  rows_zero_pads<D, REAL, P, R>(rows_smem);
   hop_rows_tile<D, REAL, P, R>(k, tile, rhs, rows_smem);
 }
 
@@ -244,9 +299,10 @@ __global__ void __launch_bounds__(RowsGeom<D, R>::NT) hop_rows_kernel(HopK k) {
 // that item's neighbour-7 barrier; the FP16 reduction array is rewritten only
 // after 8 more barriers, by which time every warp has read it.
 template <int D, bool REAL, int P, int R>
-__global__ void __launch_bounds__(RowsGeom<D, R>::NT) hop_rows_multi_kernel(const HopK *descs, const int2 *items,
+__global__ void __launch_bounds__(RowsGeom<D, REAL, R>::NT) hop_rows_multi_kernel(const HopK *descs, const int2 *items,
                                                                             int nitems, const int *frozen) {
   extern __shared__ __align__(16) unsigned char rows_smem[];
+  rows_zero_pads<D, REAL, P, R>(rows_smem);
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int2 it = items[w];
     if (frozen && frozen[it.x]) continue;
@@ -266,17 +322,18 @@ static int rows_smem_optin(F *fn, size_t bytes) {
 
 template <int D, bool REAL, int P, int R>
 int launch_rows(const HopK &k, int nrhs, cudaStream_t st) {
-  constexpr size_t sm = rows_smem_bytes<D, R, P>();
+  constexpr size_t sm = rows_smem_bytes<D, REAL, R, P>();
   static int opt = rows_smem_optin(hop_rows_kernel<D, REAL, P, R>, sm);
   if (opt != HR_OK) return opt;
   dim3 grid((unsigned)(((k.Vh + 31) / 32) * nrhs));
-  hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, R>::NT, sm, st>>>(k);
+  hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, REAL, R>::NT, sm, st>>>(k);
   return hr_check_launch("hop_rows_kernel");
 }
 
 template <int P>
 int rows_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int rows) {
   if (a.clover) return HR_ERR_UNSUPPORTED;
+  if (!a.rlinks) return HR_ERR_STATE;
   const HopK k = make_hopk(lat, a);
   const int d = lat->d;
   const bool real = lat->is_real != 0;
@@ -292,8 +349,8 @@ static const void *rows_multi_ptr(int d, int is_real, int rows, int *block, size
   const bool real = is_real != 0;
 #define HR_ROWS_CASE(DD, RE, RR)                                                  \
   if (d == DD && real == RE && rows == RR) {                                      \
-    *block = RowsGeom<DD, RR>::NT;                                                \
-    *smem = rows_smem_bytes<DD, RR, P>();                                         \
+    *block = RowsGeom<DD, RE, RR>::NT;                                            \
+    *smem = rows_smem_bytes<DD, RE, RR, P>();                                     \
     static int opt = rows_smem_optin(hop_rows_multi_kernel<DD, RE, P, RR>, *smem); \
     return opt == HR_OK ? (const void *)hop_rows_multi_kernel<DD, RE, P, RR> : nullptr; \
   }

@@ -1,5 +1,5 @@
 // Hopping kernel with the colour dimension split across a group of G threads
-// per output site, for large representations (d_R = 10 ... 35).
+// per output site, for larger representations (d_R = 6 ... 35).
 //
 // The paper notes (Sec. 3.1.2) that a one-site-per-thread kernel spills
 // registers once the represented link no longer fits, and parallelises the
@@ -254,24 +254,11 @@ static const void *multi_kernel_ptr(int d, int is_real, HopShape sh, int *block)
     return nullptr;
   }
   const int g = sh.split_g;
-  if (is_real) {
-    if (d == 8 && g == 2) return (const void *)hop_split_multi_kernel<8, true, P, 2>;
-    if (d == 8 && g == 4) return (const void *)hop_split_multi_kernel<8, true, P, 4>;
-    if (d == 15 && g == 4) return (const void *)hop_split_multi_kernel<15, true, P, 4>;
-    if (d == 15 && g == 8) return (const void *)hop_split_multi_kernel<15, true, P, 8>;
-    if (d == 24 && g == 8) return (const void *)hop_split_multi_kernel<24, true, P, 8>;
-    if (d == 24 && g == 16) return (const void *)hop_split_multi_kernel<24, true, P, 16>;
-    if (d == 35 && g == 8) return (const void *)hop_split_multi_kernel<35, true, P, 8>;
-    if (d == 35 && g == 16) return (const void *)hop_split_multi_kernel<35, true, P, 16>;
-  } else {
-    if (d == 6 && g == 2) return (const void *)hop_split_multi_kernel<6, false, P, 2>;
-    if (d == 10 && g == 2) return (const void *)hop_split_multi_kernel<10, false, P, 2>;
-    if (d == 10 && g == 4) return (const void *)hop_split_multi_kernel<10, false, P, 4>;
-    if (d == 15 && g == 4) return (const void *)hop_split_multi_kernel<15, false, P, 4>;
-    if (d == 15 && g == 8) return (const void *)hop_split_multi_kernel<15, false, P, 8>;
-    if (d == 21 && g == 4) return (const void *)hop_split_multi_kernel<21, false, P, 4>;
-    if (d == 21 && g == 8) return (const void *)hop_split_multi_kernel<21, false, P, 8>;
-  }
+  const bool real = is_real != 0;
+#define HR_SPLIT_PTR(DD, RE, GG) \
+  if (d == DD && real == RE && g == GG) return (const void *)hop_split_multi_kernel<DD, RE, P, GG>;
+  HR_SPLIT_SHAPES(HR_SPLIT_PTR)
+#undef HR_SPLIT_PTR
   return nullptr;
 }
 

@@ -42,6 +42,11 @@ struct hr_lattice {
   int nch_link;          // 2-real chunks per link
   void *links[3];        // per hr_prec
   int have_links;
+  void *rlinks[3];       // per hr_prec: rows-kernel link layout (see hr_rows_nch), or null
+  int dom;               // 1: a time slab [t0, t0 + T) of a T_global lattice (faces via halo buffers)
+  int t0, Tg;            // global time origin and extent (0 and T for a whole lattice)
+  void *halo[4];         // single-process exchange buffers: send_up, send_down, recv_up, recv_down
+  size_t halo_bytes;
   double csw;            // clover coefficient given at represent time
   void *clover_term;     // FP64 packed blocks of csw (i/4) sigma.F (no mass term)
   double clover_m0;      // m0 of the cached A and A^{-1} below
@@ -117,6 +122,7 @@ struct HopArgs {
   const void *in;         // field hopped from (parity 1-p)
   const void *self;       // field of parity p for HOP_SELF
   const void *links;      // internal links of the precision
+  const void *rlinks;     // rows-kernel layout of the same links (null if not built)
   const void *clover;     // packed A (HOP_SELF) or A^{-1} (HOP_SCALED); null = no clover
   int out_parity;
   int dagger;
@@ -126,6 +132,7 @@ struct HopArgs {
   size_t field_stride;    // bytes between rhs fields (in, out, self)
   int nrhs;
   double *norm_partials;  // optional fused |out|^2 per block (null = off)
+  int tmask;              // 1: skip the t hops that cross the slab faces (sub-domain bulk pass)
 };
 
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
@@ -158,15 +165,41 @@ static inline int hr_shape_tile(const HopShape &s) {
 // largest N of SU(N) (fundamental representation; the 2-index ones stop at 6)
 #define HR_MAX_NC 12
 
+// Rows-kernel link layout: for output parity p, direction n = 2 mu + back,
+// and output site i, the matrix V_n(x) the hop applies -- U_R,mu(x) (forward)
+// or U_R,mu(x - mu)^+ (backward) -- stored row-major at the output site, so
+// all 8 matrices of a tile of consecutive output sites are read at
+// consecutive indices: [p][n][chunk][Vh].  Complex links: chunk a*d + c holds
+// V[a][c].  Real links: rows padded to an even length dp, chunk (a*dp + c)/2
+// holds V[a][c], V[a][c+1] for even c (the pad element is 0).
+__host__ __device__ constexpr int hr_rows_dp(int d, int is_real) { return is_real ? d + (d & 1) : d; }
+__host__ __device__ constexpr int hr_rows_nch(int d, int is_real) {
+  return is_real ? d * hr_rows_dp(d, is_real) / 2 : d * d;
+}
+
 // The (d_R, rows per warp) pairs built for the rows kernel; one X(D, REAL, R)
 // line each.  Shared by the candidate list and every dispatch.
 #define HR_ROWS_SHAPES(X)                                                                               \
   X(6, false, 2) X(6, false, 3) X(7, false, 2) X(7, false, 4) X(8, false, 2) X(8, false, 4)             \
   X(8, true, 2) X(8, true, 4) X(9, false, 2) X(9, false, 3) X(10, false, 2) X(10, false, 5)             \
-  X(11, false, 3) X(11, false, 4) X(12, false, 3) X(12, false, 4) X(15, false, 3) X(15, false, 5)       \
-  X(15, true, 3) X(15, true, 5) X(21, false, 3) X(21, false, 4) X(24, true, 3) X(24, true, 4)           \
-  X(35, true, 4) X(35, true, 5)
+  X(11, false, 2) X(11, false, 3) X(12, false, 2) X(12, false, 3) X(15, false, 2) X(15, false, 3)       \
+  X(15, true, 2) X(15, true, 3) X(21, false, 2) X(21, false, 3) X(24, true, 2) X(24, true, 3)           \
+  X(35, true, 2) X(35, true, 4)
 
+
+// The (d_R, threads per site G) pairs built for the colour-split kernel.
+#define HR_SPLIT_SHAPES(X)                                                                              \
+  X(8, true, 2) X(15, true, 4) X(24, true, 8) X(35, true, 16) X(6, false, 2) X(10, false, 2)            \
+  X(12, false, 4) X(15, false, 4) X(21, false, 4)
+
+// whether the rows kernel is built for (d, real)
+static inline bool hr_has_rows_shapes(int d, int is_real) {
+#define HR_ROWS_HAS(DD, RE, RR) \
+  if (d == DD && (is_real != 0) == RE) return true;
+  HR_ROWS_SHAPES(HR_ROWS_HAS)
+#undef HR_ROWS_HAS
+  return false;
+}
 
 // Candidate shapes for (d, real, precision, several rhs); clover restricts to
 // split_g = 0.

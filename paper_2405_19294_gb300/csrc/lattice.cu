@@ -81,7 +81,20 @@ extern "C" int hr_lattice_create(int T, int L, int N, int rep, hr_lattice **out)
     hr_note_cuda_error(e, "cudaMalloc(dev_err)", __FILE__, __LINE__);
     return HR_ERR_CUDA;
   }
+  lat->t0 = 0;
+  lat->Tg = T;
   *out = lat;
+  return HR_OK;
+}
+
+extern "C" int hr_lattice_create_domain(int T_loc, int L, int N, int rep, int t0, int T_global, hr_lattice **out) {
+  if (!out) return HR_ERR_ARG;
+  *out = nullptr;
+  if (T_loc < 2 || (T_loc & 1) || t0 < 0 || (t0 & 1) || (T_global & 1) || t0 + T_loc > T_global) return HR_ERR_ARG;
+  HR_TRY(hr_lattice_create(T_loc, L, N, rep, out));
+  (*out)->dom = 1;
+  (*out)->t0 = t0;
+  (*out)->Tg = T_global;
   return HR_OK;
 }
 
@@ -90,7 +103,11 @@ void hr_cg_free(hr_lattice *lat);
 extern "C" int hr_lattice_destroy(hr_lattice *lat) {
   if (!lat) return HR_ERR_ARG;
   cudaStreamSynchronize(lat->stream);
-  for (int p = 0; p < 3; ++p) cudaFree(lat->links[p]);
+  for (int p = 0; p < 3; ++p) {
+    cudaFree(lat->links[p]);
+    cudaFree(lat->rlinks[p]);
+  }
+  for (int b = 0; b < 4; ++b) cudaFree(lat->halo[b]);
   cudaFree(lat->clover_term);
   for (int p = 0; p < 2; ++p) {
     cudaFree(lat->clover_A[p]);

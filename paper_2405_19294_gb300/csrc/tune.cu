@@ -4,11 +4,11 @@
 // size: the one-site-per-thread kernel with 32..256 threads per block
 // (register-limited occupancy changes with the block size) or the
 // colour-split kernel with G threads per site.  The first launch with a new
-// key (precision, d_R, real, clover, multi-rhs, log2 of the volume) times every
-// candidate shape with CUDA events on the caller's stream (one warm-up and
-// three timed launches each, on the caller's own buffers -- the kernel is a
-// pure function of its inputs, so repeating it is harmless) and keeps the
-// fastest.  While the stream is being captured into a CUDA graph no timing is
+// key (precision, d_R, real, clover, multi-rhs, slab, log2 of the volume)
+// times every candidate shape with CUDA events on the caller's stream (two
+// sweeps of one warm-up and four timed launches each, keeping each shape's
+// faster sweep, on the caller's own buffers -- the kernel is a pure function
+// of its inputs, so repeating it is harmless) and keeps the fastest.  While the stream is being captured into a CUDA graph no timing is
 // possible; the cached choice, else the first candidate, is used.  Setting
 // HR_TUNE=0 in the environment disables tuning (first candidate always).
 #include <map>
@@ -46,20 +46,24 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
   if (d == DD && (is_real != 0) == RE) out[n++] = HopShape{0, 32 * ((DD + RR - 1) / RR), 0, 0, RR};
     HR_ROWS_SHAPES(HR_ROWS_CAND)
 #undef HR_ROWS_CAND
-    int gs[2] = {0, 0};
-    if (is_real) {
-      if (d == 8) { gs[0] = 2; gs[1] = 4; }
-      if (d == 15) { gs[0] = 4; gs[1] = 8; }
-      if (d == 24 || d == 35) { gs[0] = 8; gs[1] = 16; }
-    } else {
-      if (d == 6) gs[0] = 2;
-      if (d == 10) { gs[0] = 2; gs[1] = 4; }
-      if (d == 15 || d == 21) { gs[0] = 4; gs[1] = 8; }
-    }
-    for (int k = 0; k < 2; ++k)
-      if (gs[k]) out[n++] = HopShape{gs[k], 128, 0, 0};
+    // colour-split kernel: every (d_R, G) pair built in hop_split.cuh
+#define HR_SPLIT_CAND(DD, RE, GG) \
+  if (d == DD && (is_real != 0) == RE) out[n++] = HopShape{GG, 128, 0, 0, 0};
+    HR_SPLIT_SHAPES(HR_SPLIT_CAND)
+#undef HR_SPLIT_CAND
   }
   return n;
+}
+
+// The candidates for this lattice: on a time slab only the site kernel, the
+// one that masks the t hops across the slab faces.
+static int lattice_shapes(const hr_lattice *lat, int prec, int clover, int multi_rhs, HopShape *out) {
+  int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, multi_rhs, out);
+  if (!lat->dom) return n;
+  int m = 0;
+  for (int k = 0; k < n; ++k)
+    if (out[k].split_g == 0 && out[k].rows == 0 && out[k].mrhs == 0) out[m++] = out[k];
+  return m;
 }
 
 static int launch_shape(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s, HopShape sh) {
@@ -78,8 +82,8 @@ static long long tune_key(const hr_lattice *lat, int prec, const HopArgs &a) {
   int lg = 0;
   while (((int64_t)1 << lg) < lat->Vh) ++lg;
   int dev = lat->device;
-  return ((((((long long)dev * 4 + prec) * 64 + lat->d) * 2 + lat->is_real) * 2 + (a.clover != nullptr)) * 2 +
-          (a.nrhs > 1)) * 64 + lg;
+  return (((((((long long)dev * 4 + prec) * 64 + lat->d) * 2 + lat->is_real) * 2 + (a.clover != nullptr)) * 2 +
+           (a.nrhs > 1)) * 2 + lat->dom) * 64 + lg;
 }
 
 static bool tuning_enabled() {
@@ -89,7 +93,7 @@ static bool tuning_enabled() {
 
 int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_t s) {
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, a.clover != nullptr, a.nrhs > 1, shapes);
+  const int n = lattice_shapes(lat, prec, a.clover != nullptr, a.nrhs > 1, shapes);
   if (n == 0) return HR_ERR_UNSUPPORTED;
   const long long key = tune_key(lat, prec, a);
   {
@@ -104,22 +108,30 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
   cudaEvent_t e0, e1;
   HR_CUDA(cudaEventCreate(&e0));
   HR_CUDA(cudaEventCreate(&e1));
+  // two sweeps over the candidates (the second in reverse order, so that no
+  // shape always runs right after the same neighbour); each candidate keeps
+  // the faster of its two timings of 4 launches
+  float t[HR_MAX_SHAPES];
+  for (int c = 0; c < n; ++c) t[c] = 1e30f;
+  for (int sweep = 0; sweep < 2; ++sweep)
+    for (int cc = 0; cc < n; ++cc) {
+      const int c = sweep ? n - 1 - cc : cc;
+      if (launch_shape(lat, prec, a, s, shapes[c]) != HR_OK) continue;  // warm-up; unsupported shapes drop out
+      HR_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 4; ++r) HR_TRY(launch_shape(lat, prec, a, s, shapes[c]));
+      HR_CUDA(cudaEventRecord(e1, s));
+      HR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      HR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < t[c]) t[c] = ms;
+    }
   float best_ms = 1e30f;
   HopShape best = shapes[0];
-  for (int c = 0; c < n; ++c) {
-    int rc = launch_shape(lat, prec, a, s, shapes[c]);  // warm-up
-    if (rc != HR_OK) continue;
-    HR_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) HR_TRY(launch_shape(lat, prec, a, s, shapes[c]));
-    HR_CUDA(cudaEventRecord(e1, s));
-    HR_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    HR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
+  for (int c = 0; c < n; ++c)
+    if (t[c] < best_ms) {
+      best_ms = t[c];
       best = shapes[c];
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
@@ -147,7 +159,7 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
 extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs, int clover, int *out, int max) {
   if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
+  const int n = lattice_shapes(lat, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n && k < max; ++k)
     out[k] = hr_shape_code(shapes[k]);
   return n;
@@ -158,7 +170,7 @@ extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs
 extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape) {
   if (!lat || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
-  const int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, nrhs > 1, shapes);
+  const int n = lattice_shapes(lat, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n; ++k)
     if (hr_shape_code(shapes[k]) == shape) {
       HopArgs a;

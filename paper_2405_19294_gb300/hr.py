@@ -75,6 +75,13 @@ _SIGS = {
                                     C.POINTER(hr_cg_params), C.POINTER(hr_cg_stats)]),
     "hr_bicgstab_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
                                     C.POINTER(hr_cg_stats)]),
+    "hr_lattice_create_domain": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "hr_domain_halo_bytes": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "hr_domain_hop_begin": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      _P, _P]),
+    "hr_domain_hop_end": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "hr_domains_dphi": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, C.c_double,
+                                  C.c_int, C.c_int, C.c_int]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -118,12 +125,18 @@ def _ptr_or_pinned(t) -> int:
 class Lattice:
     """One T x L^3 lattice of SU(N) fermions in representation ``rep`` (owns a libhr handle)."""
 
-    def __init__(self, T: int, L: int, N: int, rep: str):
+    def __init__(self, T: int, L: int, N: int, rep: str, t0: int | None = None, T_global: int | None = None):
+        """With t0 and T_global: the time slab [t0, t0 + T) of a T_global x L^3 lattice."""
         import torch
         h = _P()
-        _check(_lib.hr_lattice_create(T, L, N, REP[rep], C.byref(h)), "hr_lattice_create")
+        if t0 is None:
+            _check(_lib.hr_lattice_create(T, L, N, REP[rep], C.byref(h)), "hr_lattice_create")
+        else:
+            _check(_lib.hr_lattice_create_domain(T, L, N, REP[rep], t0, T_global, C.byref(h)),
+                   "hr_lattice_create_domain")
         self._h = h
         self.T, self.L, self.N, self.rep = T, L, N, rep
+        self.t0, self.T_global = (0, T) if t0 is None else (t0, T_global)
         info = hr_info()
         _check(_lib.hr_lattice_info(h, C.byref(info)), "hr_lattice_info")
         self.d = info.d
@@ -215,6 +228,27 @@ class Lattice:
         _check(_lib.hr_set_tuned_shape(self._h, prec, nrhs, int(clover), _shape_code(shape)),
                "hr_set_tuned_shape")
 
+    # -- time-slab sub-domain -------------------------------------------
+    def halo_bytes(self, prec: int, nrhs: int = 1) -> int:
+        n = C.c_size_t()
+        _check(_lib.hr_domain_halo_bytes(self._h, prec, nrhs, C.byref(n)), "hr_domain_halo_bytes")
+        return n.value
+
+    def new_halo(self, prec: int, nrhs: int = 1):
+        import torch
+        return torch.empty(self.halo_bytes(prec, nrhs), dtype=torch.uint8, device="cuda")
+
+    def domain_hop_begin(self, out, in_hop, self_field, out_parity: int, m0: float, prec: int, stage: int,
+                         send_up, send_down, nrhs: int = 1, dagger: bool = False):
+        sp = _ptr(self_field) if self_field is not None else None
+        _check(_lib.hr_domain_hop_begin(self._h, _ptr(out), _ptr(in_hop), sp, out_parity, m0, prec, nrhs,
+                                        int(dagger), stage, _ptr(send_up), _ptr(send_down)), "hr_domain_hop_begin")
+
+    def domain_hop_end(self, out, out_parity: int, m0: float, prec: int, stage: int, recv_up, recv_down,
+                       nrhs: int = 1, dagger: bool = False):
+        _check(_lib.hr_domain_hop_end(self._h, _ptr(out), out_parity, m0, prec, nrhs, int(dagger), stage,
+                                      _ptr(recv_up), _ptr(recv_down)), "hr_domain_hop_end")
+
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
         out = (C.c_double * nrhs)()
         _check(_lib.hr_norm2(self._h, _ptr(x), parity, prec, nrhs, out), "hr_norm2")
@@ -231,6 +265,14 @@ class Lattice:
         return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
                 "true_residual": st.true_residual, "seconds": st.seconds,
                 "hop_launches": st.hop_launches}
+
+
+def domains_dphi(lats, outs, ins, parity: int, m0: float, prec: int, nrhs: int = 1, dagger: bool = False):
+    """Dhat_p on all time slabs of one lattice held in this process (exchange by device copies)."""
+    n = len(lats)
+    arr = lambda xs: (_P * n)(*[_P(_ptr(x)) for x in xs])
+    hs = (_P * n)(*[l._h for l in lats])
+    _check(_lib.hr_domains_dphi(n, hs, arr(outs), arr(ins), parity, m0, prec, nrhs, int(dagger)), "hr_domains_dphi")
 
 
 def _shape_code(shape):

@@ -1,0 +1,114 @@
+"""Time-slab decomposition on the GPU: n slabs of one lattice (hr_domains_dphi,
+device-to-device exchange) and the begin / end entry points with
+caller-owned buffers reproduce the oracle's Dhat of the whole lattice in all
+three precisions, both parities and the adjoint."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, from_complex, oracle_operator, rel_err, to_complex
+from paper_2405_19294_gb300 import inputs, slabs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _slabs(hr, T, L, N, rep, n, eps=1.0, seed=0):
+    a = inputs.algebra_coefficients(seed, T, L, N)
+    Tl, V3 = T // n, L ** 3
+    lats = []
+    for k in range(n):
+        lat = hr.Lattice(Tl, L, N, rep, t0=k * Tl, T_global=T)
+        ak = torch.from_numpy(np.ascontiguousarray(a[k * Tl * V3:(k + 1) * Tl * V3])).cuda()
+        U = torch.empty((lat.V, 4, N, N, 2), dtype=torch.float64, device="cuda")
+        lat.links_from_algebra(U, ak, eps, True)
+        lat.represent_links(U, True, 0.0)
+        lats.append(lat)
+    return lats
+
+
+def _pack(lat, psi_slab, parity, prec):
+    f = lat.new_field(parity, prec)
+    lat.pack(f, from_complex(psi_slab), parity, prec)
+    return f
+
+
+def _unpack(lat, f, parity, prec):
+    out = torch.zeros((1, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, f, parity, prec)
+    return to_complex(out)[0]
+
+
+@pytest.mark.parametrize("N,rep", [(3, "fund"), (2, "adj"), (3, "sym"), (4, "fund")])
+@pytest.mark.parametrize("n", [1, 2, 4])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_domains_dphi_matches_oracle(hr, N, rep, n, prec):
+    T, L, m0 = 8, 4, -0.3
+    lats = _slabs(hr, T, L, N, rep, n)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    psi = inputs.gaussian_spinor(4, T, L, lats[0].d)[0]
+    V3, Tl = L ** 3, T // n
+    g = op.geom
+    for parity, dagger in ((0, 0), (1, 1), (0, 1)):
+        ins = [_pack(l, psi[None, k * Tl * V3:(k + 1) * Tl * V3], parity, prec) for k, l in enumerate(lats)]
+        outs = [l.new_field(parity, prec) for l in lats]
+        hr.domains_dphi(lats, outs, ins, parity, m0, prec, dagger=bool(dagger))
+        got = np.concatenate([_unpack(l, outs[k], parity, prec) for k, l in enumerate(lats)])
+        ref = op.apply_schur(psi, parity, dagger=bool(dagger))
+        mask = g.parity == parity
+        assert rel_err(got, ref, mask) < TOL[prec], (parity, dagger)
+        assert np.all(got[~mask] == 0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_slab_dirac_begin_end_two_slabs_one_process(hr, prec):
+    """The caller-owned-buffer path: two slabs, the exchange done by hand."""
+    T, L, N, rep, m0 = 8, 6, 3, "fund", -0.4
+    lats = _slabs(hr, T, L, N, rep, 2)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    psi = inputs.gaussian_spinor(5, T, L, N)[0]
+    V3, Tl = L ** 3, T // 2
+    ins = [_pack(l, psi[None, k * Tl * V3:(k + 1) * Tl * V3], 0, prec) for k, l in enumerate(lats)]
+    tmps = [l.new_field(1, prec) for l in lats]
+    outs = [l.new_field(0, prec) for l in lats]
+    bufs = [[l.new_halo(prec) for _ in range(4)] for l in lats]
+    for stage in (0, 1):
+        for k, l in enumerate(lats):
+            o, ih = (tmps[k], ins[k]) if stage == 0 else (outs[k], tmps[k])
+            l.domain_hop_begin(o, ih, ins[k] if stage else None, 1 - stage, m0, prec, stage,
+                               bufs[k][0], bufs[k][1])
+        for k in range(2):
+            bufs[k][2].copy_(bufs[(k + 1) % 2][1])   # receive-up <- send-down of the slab above
+            bufs[k][3].copy_(bufs[(k + 1) % 2][0])   # receive-down <- send-up of the slab below
+        for k, l in enumerate(lats):
+            o = tmps[k] if stage == 0 else outs[k]
+            l.domain_hop_end(o, 1 - stage, m0, prec, stage, bufs[k][2], bufs[k][3])
+    got = np.concatenate([_unpack(l, outs[k], 0, prec) for k, l in enumerate(lats)])
+    ref = op.apply_schur(psi, 0)
+    assert rel_err(got, ref, op.geom.parity == 0) < TOL[prec]
+
+
+def test_slab_dirac_single_rank(hr):
+    """slabs.SlabDirac on one rank (one slab covering the lattice) equals hr_dphi."""
+    T, L, N, rep, m0 = 8, 4, 3, "sym", -0.3
+    lat = _slabs(hr, T, L, N, rep, 1)[0]
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    psi = inputs.gaussian_spinor(6, T, L, lat.d)[0]
+    f = _pack(lat, psi[None], 0, 1)
+    out = lat.new_field(0, 1)
+    slabs.SlabDirac(lat, prec=1).apply(out, f, 0, m0)
+    assert rel_err(_unpack(lat, out, 0, 1), op.apply_schur(psi, 0), op.geom.parity == 0) < TOL[1]
+
+
+def test_slab_errors(hr):
+    with pytest.raises(hr.HrError):
+        hr.Lattice(3, 4, 3, "fund", t0=0, T_global=8)      # odd slab
+    with pytest.raises(hr.HrError):
+        hr.Lattice(4, 4, 3, "fund", t0=6, T_global=8)      # past the end
+    lats = _slabs(hr, 8, 4, 3, "fund", 2)
+    f = [l.new_field(0, 1) for l in lats]
+    with pytest.raises(hr.HrError):
+        hr.domains_dphi(lats[::-1], [l.new_field(0, 1) for l in lats[::-1]], f[::-1], 0, -0.3, 1)  # out of order
+    lat = hr.Lattice(4, 4, 3, "fund", t0=0, T_global=8)
+    U = torch.zeros((lat.V, 4, 3, 3, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(hr.HrError):
+        lat.represent_links(U, False, 1.0)                  # clover on a slab
