@@ -296,7 +296,61 @@ def run_suite(args):
         out.append(_suite_c4(hr, inputs, torch))
     if "largen" in which:
         out.extend(_suite_large_nc(hr, inputs, torch))
+    if "larged" in which:
+        out.extend(_suite_large_d(hr, inputs, torch))
     return out
+
+
+def _suite_large_d(hr, inputs, torch):
+    """Every launch shape of the large representations (d_R = 8 ... 35), FP32 Dhat
+    at 32 x 16^3 (and FP16 / FP64 for SU(6) adjoint), cold L2 between steps."""
+    m0 = -0.4
+    flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+    lines = []
+    for N, rep, prec in ((3, "adj", hr.F32), (4, "sym", hr.F32), (6, "asym", hr.F32), (4, "adj", hr.F32),
+                         (6, "sym", hr.F32), (5, "adj", hr.F32), (6, "adj", hr.F32), (6, "adj", hr.F16),
+                         (6, "sym", hr.F16), (6, "adj", hr.F64)):
+        T, L = 32, 16
+        lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+        fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
+        fo = lat.new_field(0, prec)
+        w = {hr.F64: 8, hr.F32: 4, hr.F16: 2}[prec]
+        bytes_ = bytes_per_even_site(N, rep, w) * lat.Vh
+        shapes = {}
+        for sh in lat.shape_candidates(prec):
+            lat.set_shape(prec, sh)
+            ms = _time_dhat(lat, fi, fo, m0, prec, torch, flush)
+            fam = "site" if (sh[0] == 0 and sh[4] == 0) else ("rows" if sh[4] else "split")
+            shapes[str(tuple(sh))] = {"family": fam, "ms": round(ms, 4), "GBs": round(bytes_ / ms / 1e6, 1)}
+        best = {}
+        for k, v in shapes.items():
+            if v["family"] not in best or v["ms"] < best[v["family"]]["ms"]:
+                best[v["family"]] = dict(v, shape=k)
+        line = {"suite": "large d_R, Dhat at 16^3x32, every launch shape", "N": N, "rep": rep, "d": lat.d,
+                "prec": ("fp64", "fp32", "fp16")[prec], "best_per_family": best, "shapes": shapes}
+        print(json.dumps(line), flush=True)
+        lines.append(line)
+        lat.close()
+        del fi, fo
+        torch.cuda.empty_cache()
+    return lines
+
+
+def run_one_dhat(spec):
+    """A single pinned-shape Dhat case for ncu captures: three applications, no timing."""
+    import torch
+    from paper_2405_19294_gb300 import hr, inputs
+    N, rep, T, L, prec, shape = spec.split(",")
+    N, T, L = int(N), int(T), int(L)
+    prec = {"f64": hr.F64, "f32": hr.F32, "f16": hr.F16}[prec]
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+    fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
+    fo = lat.new_field(0, prec)
+    lat.set_shape(prec, tuple(int(v) for v in shape.split(":")))
+    for _ in range(3):
+        lat.dphi(fo, fi, 0, -0.4, 0.0, prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"one_dhat": spec, "d": lat.d, "shape": lat.tuned_shape(prec)}))
 
 
 def _large_nc_geometry(N, target_bytes):
@@ -484,11 +538,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen: measure those workloads instead")
+    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen,larged: measure those workloads instead")
     ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
     ap.add_argument("--L", type=int, default=WORKLOAD["L"], help="space extent (profiling runs only)")
+    ap.add_argument("--one-dhat", default="", metavar="N,REP,T,L,PREC,SHAPE",
+                    help="profiling case: build one lattice (PREC f64/f32/f16), pin the launch shape "
+                         "SHAPE = G:block:regs:mrhs:rows and apply Dhat three times, nothing else")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -497,6 +554,9 @@ def main():
         return
     if args.suite:
         run_suite(args)
+        return
+    if args.one_dhat:
+        run_one_dhat(args.one_dhat)
         return
 
     import torch
@@ -574,29 +634,64 @@ def main():
     b64 = bytes_per_even_site(N, rep, 8) * sites
     fl = flops_per_even_site(N, rep) * sites
 
-    # end to end through the C ABI with host buffers: the canonical FP64 source
-    # and result live in page-locked host memory; one DMA copy each way around
-    # pack -> Dhat -> unpack.  (The library can also read / write page-locked
-    # host memory in place -- only the parity's sites cross the host link -- but
+    # end to end through the C ABI with host buffers: every step copies the
+    # canonical FP64 source from page-locked host memory to the device
+    # (DMA), packs it, applies Dhat, unpacks and copies the result back to
+    # page-locked host memory.  Steps are pipelined the way a serving loop
+    # would run them: the copies go on their own streams with double-buffered
+    # device staging, so the host-to-device copy of step k+1 and the
+    # device-to-host copy of step k-1 overlap step k's kernels (the host link
+    # is full duplex); the kernels of successive steps stay in order on the
+    # lattice's stream.  (The library can also read / write page-locked host
+    # memory in place -- only the parity's sites cross the host link -- but
     # per-thread scattered reads over the host link measured slower than one
     # bulk DMA copy of the whole field for this layout.)
-    out_host = torch.empty_like(src_host).pin_memory()
-    dev_in = torch.empty_like(src)
-    dev_out = torch.zeros_like(src)
-    e2e_ms = []
-    for k in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dev_in.copy_(src_host, non_blocking=True)
-        lat.pack(fin[hr.F32], dev_in, hr.EVEN, hr.F32)
-        lat.dphi(fout[hr.F32], fin[hr.F32], hr.EVEN, m0, csw, hr.F32)
-        lat.unpack(dev_out, fout[hr.F32], hr.EVEN, hr.F32)
-        out_host.copy_(dev_out, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e = float(np.mean(e2e_ms))
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    out_host = [torch.empty_like(src_host).pin_memory() for _ in range(2)]
+    dev_in = [torch.empty_like(src) for _ in range(2)]
+    dev_out = [torch.zeros_like(src) for _ in range(2)]
+    ev = lambda: torch.cuda.Event()
+    packed = [ev(), ev()]      # dev_in[b] consumed by pack
+    landed = [ev(), ev()]      # dev_in[b] filled
+    done = [ev(), ev()]        # dev_out[b] filled
+    drained = [ev(), ev()]     # dev_out[b] copied out
+    for b in range(2):
+        packed[b].record(stream)
+        drained[b].record(stream)
+
+    def e2e_run(nsteps):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        s_h2d.wait_stream(stream)
+        s_d2h.wait_stream(stream)
+        for k in range(nsteps):
+            b = k % 2
+            with torch.cuda.stream(s_h2d):
+                s_h2d.wait_event(packed[b])
+                dev_in[b].copy_(src_host, non_blocking=True)
+                landed[b].record(s_h2d)
+            stream.wait_event(landed[b])
+            lat.pack(fin[hr.F32], dev_in[b], hr.EVEN, hr.F32)
+            packed[b].record(stream)
+            lat.dphi(fout[hr.F32], fin[hr.F32], hr.EVEN, m0, csw, hr.F32)
+            stream.wait_event(drained[b])
+            lat.unpack(dev_out[b], fout[hr.F32], hr.EVEN, hr.F32)
+            done[b].record(stream)
+            with torch.cuda.stream(s_d2h):
+                s_d2h.wait_event(done[b])
+                out_host[b].copy_(dev_out[b], non_blocking=True)
+                drained[b].record(s_d2h)
+        stream.wait_stream(s_h2d)
+        stream.wait_stream(s_d2h)
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1) / nsteps
+
+    e2e_run(args.warmup)
+    e2e = e2e_run(args.steps)
+    out_host = out_host[(args.steps - 1) % 2]
     h2d = src_host.numel() * 8
     d2h = out_host.numel() * 8
 
@@ -638,7 +733,9 @@ def main():
             "roofline": roof,
             "gpu_launches": 2 * args.steps,
             "e2e": {"value": round(world * b32 / (e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e, 3)},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e, 3),
+                    "mode": "steps pipelined: host-to-device of step k+1 and device-to-host of step k-1 "
+                            "overlap step k's kernels (copy streams, double-buffered staging)"},
             "fp64": {"ms_per_step": round(ms64, 4), "gbs": round(b64 / (ms64 * 1e-3) / 1e9, 2),
                      "tflops": round(fl / (ms64 * 1e-3) / 1e12, 3), "bound": "alu (FP64)"},
             "cg": cg, "clocks": clk, "wall_timed_s": round(wall, 3)}

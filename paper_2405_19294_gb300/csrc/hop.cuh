@@ -29,12 +29,13 @@ struct HopK {
   const void *in;
   const void *self;
   const void *links;
-  const void *rlinks;
   const void *clover;
-  int T, L, Lh, p, mode, nch, nrhs, tmask;
+  int T, L, Lh, p, mode, nch, nrhs;
   int64_t Vh;
   size_t stride;
   double sgn, coef, diag;
+  const void *rlinks;  // rows-kernel link layout (rows kernel only)
+  int tmask;           // time-slab bulk pass (site kernel only)
 };
 
 // Blocks are numbered right-hand side fastest: block b handles tile b / nrhs
@@ -184,8 +185,11 @@ __device__ __forceinline__ void clover_apply(const void *cl, int64_t Vh, int64_t
   }
 }
 
-// The whole stencil for output site i (< Vh) of right-hand side rhs.
-template <int D, bool REAL, int P>
+// The whole stencil for output site i (< Vh) of right-hand side rhs.  MASK:
+// on a time slab, leave out the t hops that cross its faces (they arrive
+// later from the halo); a template flag so that the ordinary kernels carry no
+// branch that would keep the compiler from hoisting the t-direction loads.
+template <int D, bool REAL, int P, bool MASK = false>
 __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
   typedef typename PT<P>::A A;
   const size_t roff = (size_t)rhs * k.stride;
@@ -213,9 +217,9 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
   {
     const int tf = (s.t + 1 == T) ? 0 : s.t + 1, tb = (s.t == 0) ? T - 1 : s.t - 1;
     const int64_t jf = i + (int64_t)(tf - s.t) * L * LLh, jb = i + (int64_t)(tb - s.t) * L * LLh;
-    if (!(k.tmask && s.t == T - 1))
+    if (!(MASK && s.t == T - 1))
       hop_dir<D, REAL, P, 0, false>(acc, in, Vh, jf, slot(p, 0), i, -sg, P == 2 ? (A)isc[jf] : A(1));
-    if (!(k.tmask && s.t == 0))
+    if (!(MASK && s.t == 0))
       hop_dir<D, REAL, P, 0, true>(acc, in, Vh, jb, slot(1 - p, 0), jb, sg, P == 2 ? (A)isc[jb] : A(1));
   }
   // mu = 1 (x)
@@ -300,13 +304,13 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 // Register budget variants (the autotuner picks one with the block size):
 // MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
 // loads in flight per thread) and 64 x 12 (at most ~85 registers: more warps).
-template <int D, bool REAL, int P, int MAXT, int MINB>
+template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false>
 __global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k) {
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
   const int64_t i = tile * blockDim.x + threadIdx.x;
-  if (i < k.Vh) hop_site<D, REAL, P>(k, i, rhs);
+  if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
 }
 
 // Persistent multi-lattice form: every block walks the work list (lattice,
@@ -351,7 +355,8 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
 
 template <int D, bool REAL, int P>
 static void launch_site(const HopK &k, dim3 grid, int bs, int variant, cudaStream_t st) {
-  if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k);
+  if (k.tmask) hop_kernel<D, REAL, P, 256, 1, true><<<grid, bs, 0, st>>>(k);  // time-slab bulk pass
+  else if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k);
   else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k);
   else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k);
 }

@@ -55,14 +55,15 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
   return n;
 }
 
-// The candidates for this lattice: on a time slab only the site kernel, the
-// one that masks the t hops across the slab faces.
+// The candidates for this lattice: on a time slab only the site kernel with
+// the compiler's register choice, the one built to mask the t hops across the
+// slab faces.
 static int lattice_shapes(const hr_lattice *lat, int prec, int clover, int multi_rhs, HopShape *out) {
   int n = hr_hop_shapes(lat->d, lat->is_real, prec, clover, multi_rhs, out);
   if (!lat->dom) return n;
   int m = 0;
   for (int k = 0; k < n; ++k)
-    if (out[k].split_g == 0 && out[k].rows == 0 && out[k].mrhs == 0) out[m++] = out[k];
+    if (out[k].split_g == 0 && out[k].rows == 0 && out[k].mrhs == 0 && out[k].regs == 0) out[m++] = out[k];
   return m;
 }
 
