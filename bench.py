@@ -298,7 +298,39 @@ def run_suite(args):
         out.extend(_suite_large_nc(hr, inputs, torch))
     if "larged" in which:
         out.extend(_suite_large_d(hr, inputs, torch))
+    if "blas" in which:
+        out.append(_suite_blas(hr, inputs, torch))
     return out
+
+
+def _suite_blas(hr, inputs, torch):
+    """Reduction bandwidth (Sec. 3.2): hr_norm2 over 12 even-parity SU(3) fields of 32^3 x 64
+    per precision, wall time per call (it returns the sums to the host), cold L2."""
+    T, L, N, rep, nr = 64, 32, 3, "fund", 12
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+    flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+    peak = measured_peaks()[0]["hbm_gbs"]
+    line = {"suite": "norm2 of 12 even-parity SU(3) fund fields, 32^3x64, FP64 accumulation", "fields": nr}
+    for name, prec in (("fp64", hr.F64), ("fp32", hr.F32), ("fp16", hr.F16)):
+        f = lat.new_field(0, prec, nr)
+        f.zero_()                  # contents do not matter for the timing
+        nbytes = lat.field_bytes(0, prec, nr)
+        for _ in range(3):
+            lat.norm2(f, 0, prec, nr)
+        ts = []
+        for _ in range(10):
+            flush.sum()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.norm2(f, 0, prec, nr)
+            ts.append(time.perf_counter() - t0)
+        dt = float(np.median(ts))
+        line[name] = {"bytes": nbytes, "ms": round(dt * 1e3, 4), "GBs": round(nbytes / dt / 1e9, 1),
+                      "frac_of_measured_copy": round(nbytes / dt / 1e9 / peak, 3)}
+        del f
+    print(json.dumps(line), flush=True)
+    lat.close()
+    return line
 
 
 def _suite_large_d(hr, inputs, torch):
@@ -525,6 +557,14 @@ def _suite_c4(hr, inputs, torch):
             "max_true_residual": max(s_["true_residual"] for s_ in st),
             "iterations_sum": its, "site_iterations_per_s_batched": round(sum(
                 (T * L ** 3 // 2) * s_["iterations"] for (T, L, N, rep), s_ in zip(shapes, st)) / tb, 1)}
+    # model bytes of the operator applications (ideal reuse): two FP32 Dhat per inner
+    # iteration, two FP64 Dhat per outer true residual; their rate against the batched time
+    b_in = sum(2 * s_["iterations"] * bytes_per_even_site(N, rep, 4) * (T * L ** 3 // 2)
+               for (T, L, N, rep), s_ in zip(shapes, st))
+    b_out = sum(2 * s_["outer_steps"] * bytes_per_even_site(N, rep, 8) * (T * L ** 3 // 2)
+                for (T, L, N, rep), s_ in zip(shapes, st))
+    line["operator_model_gb"] = {"fp32_inner": round(b_in / 1e9, 2), "fp64_outer": round(b_out / 1e9, 2)}
+    line["operator_model_gbs_batched"] = round((b_in + b_out) / tb / 1e9, 1)
     print(json.dumps(line), flush=True)
     batch.close()
     return line
@@ -538,7 +578,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen,larged: measure those workloads instead")
+    ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen,larged,blas: measure those workloads instead")
     ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")

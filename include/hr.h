@@ -6,10 +6,11 @@
  * The paper ("GPU-accelerated Higher Representations of Wilson Fermions with
  * HiRep") provides, on GPUs, the Wilson-Dirac operator for general higher
  * representations of SU(N_c), single and double precision, even-odd
- * preconditioning and clover improvement (Sec. 3.1), the spin projection to
- * half-spinors (Sec. 2.2), site-wise linear algebra and reductions
- * (Sec. 3.2) and the conjugate-gradient inverter (Sec. 3.3).  It prints no
- * formula; this library implements the standard definitions:
+ * preconditioning, clover improvement and its exponentiated form (Sec. 3.1),
+ * the spin projection to half-spinors and the bulk / receive-buffer geometry
+ * with half-spinor sends (Sec. 2), site-wise linear algebra and reductions
+ * (Sec. 3.2) and the conjugate-gradient and BiCGstab inverters (Sec. 3.3).
+ * It prints no formula; this library implements the standard definitions:
  *
  *   D psi(x) = A(x) psi(x) - 1/2 sum_mu [ (1 - g_mu) U_R,mu(x) psi(x+mu)
  *                                       + (1 + g_mu) U_R,mu(x-mu)^+ psi(x-mu) ]
@@ -94,6 +95,21 @@ typedef struct {
   double seconds;      /* wall time of the call */
   double hop_launches; /* hopping-kernel launches issued */
 } hr_cg_stats;
+
+/* ---- device memory ------------------------------------------------------ */
+
+/* Allocator for the library's large device buffers (represented links in all
+ * precisions, the rows layout, clover blocks, the Schur intermediate, solver
+ * workspaces, slab face buffers), e.g. PyTorch's caching allocator.  alloc
+ * returns device memory of at least `bytes` on the current device (256-byte
+ * aligned; NULL on failure -> HR_ERR_NOMEM) and release frees it; each block
+ * is released through the function pair it was allocated with, so the
+ * allocator may be changed at any time.  NULL, NULL restores cudaMalloc /
+ * cudaFree.  Small control words stay on cudaMalloc.  Process-wide.
+ * Errors: HR_ERR_ARG (only one of the two given). */
+typedef void *(*hr_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*hr_free_fn)(void *ptr, size_t bytes, void *ctx);
+int hr_set_allocator(hr_alloc_fn alloc, hr_free_fn release, void *ctx);
 
 /* ---- lattice handle --------------------------------------------------- */
 

@@ -296,12 +296,13 @@ static int bi_work(int prec, size_t bytes) {
     HR_CUDA(cudaStreamCreateWithFlags(&g_bi->s, cudaStreamNonBlocking));
   }
   if (g_bi->cap[prec] < bytes) {
+    HR_CUDA(cudaDeviceSynchronize());
     for (int k = 0; k < 8; ++k) {
-      cudaFree(g_bi->f[prec][k]);
+      hr_dev_free(g_bi->f[prec][k]);
       g_bi->f[prec][k] = nullptr;
     }
     g_bi->cap[prec] = 0;
-    for (int k = 0; k < 8; ++k) HR_CUDA(cudaMalloc(&g_bi->f[prec][k], bytes));
+    for (int k = 0; k < 8; ++k) HR_TRY(hr_dev_alloc(&g_bi->f[prec][k], bytes));
     g_bi->cap[prec] = bytes;
   }
   return HR_OK;

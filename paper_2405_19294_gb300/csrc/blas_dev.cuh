@@ -110,14 +110,14 @@ __device__ __forceinline__ double norm2_sites(const char *base, int64_t Vh, int 
   typedef typename PT<P>::A A;
   double acc = 0.0;
   for (int64_t i = i0; i < Vh; i += stride) {
-    A s = 0;
+    A s[4] = {0, 0, 0, 0};  // one chain per spin: four independent FMA chains (GB300's FP64 latency)
     for (int c = 0; c < d; ++c) {
       cx<A> v[4];
       ld_colour<P>(base, Vh, i, c, v);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s += v[q].x * v[q].x + v[q].y * v[q].y;
+      for (int q = 0; q < 4; ++q) s[q] = fma(v[q].y, v[q].y, fma(v[q].x, v[q].x, s[q]));
     }
-    double sd = (double)s;
+    double sd = (double)((s[0] + s[1]) + (s[2] + s[3]));
     if (P == 2) {
       const double sc = (double)f16_scales(base, Vh, d)[i];
       sd *= sc * sc;
@@ -134,7 +134,7 @@ __device__ __forceinline__ double cg_xr_sites(char *xb, char *rb, const char *pb
   typedef typename PT<PR>::A AR;
   double acc = 0.0;
   for (int64_t i = i0; i < Vh; i += stride) {
-    AR s = 0;
+    AR s[4] = {0, 0, 0, 0};  // one chain per spin
     for (int c = 0; c < d; ++c) {
       cx<AR> xv[4], rv[4];
       cx<typename PT<PP>::A> pv[4], av[4];
@@ -146,12 +146,12 @@ __device__ __forceinline__ double cg_xr_sites(char *xb, char *rb, const char *pb
       for (int q = 0; q < 4; ++q) {
         xv[q] = mk(fma(al, (AR)pv[q].x, xv[q].x), fma(al, (AR)pv[q].y, xv[q].y));
         rv[q] = mk(fma(-al, (AR)av[q].x, rv[q].x), fma(-al, (AR)av[q].y, rv[q].y));
-        s += rv[q].x * rv[q].x + rv[q].y * rv[q].y;
+        s[q] = fma(rv[q].y, rv[q].y, fma(rv[q].x, rv[q].x, s[q]));
       }
       stc<PR>(xb, Vh, i, c, xv, 1.f);
       stc<PR>(rb, Vh, i, c, rv, 1.f);
     }
-    acc += (double)s;
+    acc += (double)((s[0] + s[1]) + (s[2] + s[3]));
   }
   return acc;
 }
@@ -217,7 +217,7 @@ __device__ __forceinline__ double axpby_sites(const char *xb, char *yb, int64_t 
       }
       inv = m > 0.f ? 1.f / m : 0.f;
     }
-    AY s = 0;
+    AY s[4] = {0, 0, 0, 0};  // one chain per spin
     for (int c = 0; c < d; ++c) {
       cx<typename PT<PX>::A> xv[4];
       cx<AY> yv[4];
@@ -230,12 +230,12 @@ __device__ __forceinline__ double axpby_sites(const char *xb, char *yb, int64_t 
       for (int q = 0; q < 4; ++q) {
         if (PY == 2) yv[q] = mk(av * (AY)xv[q].x + bv * yv[q].x, av * (AY)xv[q].y + bv * yv[q].y);
         else yv[q] = mk(fma(av, (AY)xv[q].x, bv * yv[q].x), fma(av, (AY)xv[q].y, bv * yv[q].y));
-        s += yv[q].x * yv[q].x + yv[q].y * yv[q].y;
+        s[q] = fma(yv[q].y, yv[q].y, fma(yv[q].x, yv[q].x, s[q]));
       }
       stc<PY>(yb, Vh, i, c, yv, inv);
     }
     if (PY == 2) f16_scales_w(yb, Vh, d)[i] = m;
-    acc += (double)s;
+    acc += (double)((s[0] + s[1]) + (s[2] + s[3]));
   }
   return acc;
 }

@@ -43,7 +43,7 @@ void hr_cg_free(hr_lattice *lat) {
   hr_cg_work *w = lat->cg;
   if (!w) return;
   for (int p = 0; p < 3; ++p)
-    for (int q = 0; q < 6; ++q) cudaFree(w->f[p][q]);
+    for (int q = 0; q < 6; ++q) hr_dev_free(w->f[p][q]);
   cudaFree(w->scal);
   cudaFree(w->iters);
   cudaFreeHost(w->host);
@@ -66,11 +66,11 @@ static int cg_work(hr_lattice *lat, int prec, size_t bytes) {
   hr_cg_work *w = lat->cg;
   if (w->cap[prec] < bytes) {
     for (int q = 0; q < 6; ++q) {
-      cudaFree(w->f[prec][q]);
+      hr_dev_free(w->f[prec][q]);
       w->f[prec][q] = nullptr;
     }
     w->cap[prec] = 0;
-    for (int q = 0; q < 6; ++q) HR_CUDA(cudaMalloc(&w->f[prec][q], bytes));
+    for (int q = 0; q < 6; ++q) HR_TRY(hr_dev_alloc(&w->f[prec][q], bytes));
     w->cap[prec] = bytes;
   }
   return HR_OK;

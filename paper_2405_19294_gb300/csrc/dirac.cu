@@ -23,10 +23,11 @@ __device__ __forceinline__ zd zmul2(zd a, zd b) { return mk(a.x * b.x - a.y * b.
 
 int hr_ensure_tmp(hr_lattice *lat, size_t bytes) {
   if (lat->tmp_bytes >= bytes) return HR_OK;
-  cudaFree(lat->tmp);
+  cudaStreamSynchronize(lat->stream);
+  hr_dev_free(lat->tmp);
   lat->tmp = nullptr;
   lat->tmp_bytes = 0;
-  HR_CUDA(cudaMalloc(&lat->tmp, bytes));
+  HR_TRY(hr_dev_alloc(&lat->tmp, bytes));
   lat->tmp_bytes = bytes;
   return HR_OK;
 }
@@ -186,7 +187,7 @@ int hr_clover_build(hr_lattice *lat) {
   if (lat->d > HR_CLOVER_MAX_D) return HR_ERR_UNSUPPORTED;
   const int d = lat->d;
   const size_t bytes = (size_t)2 * 4 * d * d * (size_t)lat->Vh * 16u;
-  if (!lat->clover_term) HR_CUDA(cudaMalloc(&lat->clover_term, bytes));
+  if (!lat->clover_term) HR_TRY(hr_dev_alloc(&lat->clover_term, bytes));
   ClK k;
   k.T = lat->T;
   k.L = lat->L;
@@ -338,8 +339,8 @@ int hr_clover_prepare(hr_lattice *lat, double m0) {
   const int d = lat->d;
   const size_t n64 = (size_t)2 * 4 * d * d * (size_t)lat->Vh * 16u;
   for (int q = 0; q < 2; ++q) {
-    if (!lat->clover_A[q]) HR_CUDA(cudaMalloc(&lat->clover_A[q], q == 0 ? n64 : n64 / 2));
-    if (!lat->clover_Ainv[q]) HR_CUDA(cudaMalloc(&lat->clover_Ainv[q], q == 0 ? n64 : n64 / 2));
+    if (!lat->clover_A[q]) HR_TRY(hr_dev_alloc(&lat->clover_A[q], q == 0 ? n64 : n64 / 2));
+    if (!lat->clover_Ainv[q]) HR_TRY(hr_dev_alloc(&lat->clover_Ainv[q], q == 0 ? n64 : n64 / 2));
   }
   ClK k;
   memset(&k, 0, sizeof(k));

@@ -362,7 +362,7 @@ static int hr_rows_links_build(hr_lattice *lat, const RepK &k) {
   const size_t es[3] = {16, 8, 4};
   for (int p = 0; p < 3; ++p) {
     if (!lat->rlinks[p])
-      HR_CUDA(cudaMalloc(&lat->rlinks[p], (nrows + HR_ROWS_SLACK) * (size_t)lat->Vh * es[p]));
+      HR_TRY(hr_dev_alloc(&lat->rlinks[p], (nrows + HR_ROWS_SLACK) * (size_t)lat->Vh * es[p]));
     HR_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(lat->rlinks[p]) + nrows * (size_t)lat->Vh * es[p], 0,
                             (size_t)HR_ROWS_SLACK * lat->Vh * es[p], lat->stream));
   }
@@ -378,7 +378,7 @@ extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reun
   const size_t nchunks = (size_t)2 * 4 * lat->nch_link * (size_t)lat->Vh;
   const size_t es[3] = {16, 8, 4};
   for (int p = 0; p < 3; ++p)
-    if (!lat->links[p]) HR_CUDA(cudaMalloc(&lat->links[p], nchunks * es[p]));
+    if (!lat->links[p]) HR_TRY(hr_dev_alloc(&lat->links[p], nchunks * es[p]));
   RepK k;
   k.T = lat->T;
   k.L = lat->L;

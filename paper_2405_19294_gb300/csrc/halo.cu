@@ -350,12 +350,13 @@ extern "C" int hr_domains_dphi(int n, hr_lattice *const *lats, void *const *out,
   for (int k = 0; k < n; ++k) {
     hr_lattice *l = lats[k];
     if (l->halo_bytes < hb) {
+      HR_CUDA(cudaStreamSynchronize(s));
       for (int b = 0; b < 4; ++b) {
-        cudaFree(l->halo[b]);
+        hr_dev_free(l->halo[b]);
         l->halo[b] = nullptr;
       }
       l->halo_bytes = 0;
-      for (int b = 0; b < 4; ++b) HR_CUDA(cudaMalloc(&l->halo[b], hb));
+      for (int b = 0; b < 4; ++b) HR_TRY(hr_dev_alloc(&l->halo[b], hb));
       l->halo_bytes = hb;
     }
     HR_TRY(hr_ensure_tmp(l, hr_spinor_field_bytes(l->Vh, l->d, prec) * (size_t)nrhs));

@@ -82,6 +82,29 @@ __device__ __forceinline__ void reconstruct(R sig, cx<R> r0, cx<R> r1, cx<R> acc
   }
 }
 
+// reconstruct with the neighbour's FP16 site scale w folded in:
+// acc += w * (rebuilt 4-spinor), the scale riding on the FMAs that add the
+// rows anyway instead of a separate multiply of the half-spinor.
+template <int MU, typename R>
+__device__ __forceinline__ void reconstruct_w(R sig, R w, cx<R> r0, cx<R> r1, cx<R> acc[4]) {
+  const R sw = sig * w;
+  acc[0] = axpy_r(w, r0, acc[0]);
+  acc[1] = axpy_r(w, r1, acc[1]);
+  if (MU == 0) {
+    acc[2] = axpy_r(-sw, r0, acc[2]);
+    acc[3] = axpy_r(-sw, r1, acc[3]);
+  } else if (MU == 1) {
+    acc[2] = axpy_i(sw, r1, acc[2]);
+    acc[3] = axpy_i(sw, r0, acc[3]);
+  } else if (MU == 2) {
+    acc[2] = axpy_r(sw, r1, acc[2]);
+    acc[3] = axpy_r(-sw, r0, acc[3]);
+  } else {
+    acc[2] = axpy_i(sw, r0, acc[2]);
+    acc[3] = axpy_i(-sw, r1, acc[3]);
+  }
+}
+
 // One direction, one side: project psi(j), multiply by U (or U^+ when ADJ),
 // accumulate.  `lk` points at chunk 0 of the link slot, `li` is the link's
 // site index in that slot.
@@ -90,17 +113,18 @@ __device__ __forceinline__ void hop_dir(cx<typename PT<P>::A> acc[D][4], const v
                                         int64_t j, const void *lk, int64_t li,
                                         typename PT<P>::A sig, typename PT<P>::A scl) {
   typedef typename PT<P>::A A;
+  // FP16: the neighbour's site scale scl is applied in the reconstruction
   cx<A> h0[D], h1[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     cx<A> psi[4];
     ld_colour<P>(in, Vh, j, c, psi);
     project<MU>(sig, psi, h0[c], h1[c]);
-    if (P == 2) {
-      h0[c] = scale(scl, h0[c]);
-      h1[c] = scale(scl, h1[c]);
-    }
   }
+  auto rebuild = [&](cx<A> r0, cx<A> r1, cx<A> a4[4]) {
+    if (P == 2) reconstruct_w<MU>(sig, scl, r0, r1, a4);
+    else reconstruct<MU>(sig, r0, r1, a4);
+  };
   if (REAL) {
     constexpr int NC = (D * D + 1) / 2;
     cx<A> u[NC];
@@ -116,7 +140,7 @@ __device__ __forceinline__ void hop_dir(cx<typename PT<P>::A> acc[D][4], const v
         r0 = rfma(ue, h0[c], r0);
         r1 = rfma(ue, h1[c], r1);
       }
-      reconstruct<MU>(sig, r0, r1, acc[a]);
+      rebuild(r0, r1, acc[a]);
     }
   } else {
 #pragma unroll
@@ -134,7 +158,7 @@ __device__ __forceinline__ void hop_dir(cx<typename PT<P>::A> acc[D][4], const v
           r1 = cfma(ue, h1[c], r1);
         }
       }
-      reconstruct<MU>(sig, r0, r1, acc[a]);
+      rebuild(r0, r1, acc[a]);
     }
   }
 }
@@ -259,7 +283,7 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       ld_colour<P>(self, Vh, i, c, sv[c]);
-      if (P == 2)
+      if (P == 2 && k.clover)  // without clover the scale joins the diagonal factor below
 #pragma unroll
         for (int q = 0; q < 4; ++q) sv[c][q] = scale(ssc, sv[c][q]);
     }
@@ -270,7 +294,7 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[c][q] = acc[c][q] + sv[c][q];
     } else {
-      const A dg = (A)k.diag;
+      const A dg = (A)k.diag * ssc;
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll

@@ -38,14 +38,21 @@ struct RowsGeom {
   static constexpr int DC = (D + CB - 1) / CB * CB;                        // staged colours (padded)
   static constexpr int DP = hr_rows_dp(D, REAL);
   static constexpr int NCH = hr_rows_nch(D, REAL);
+  // neighbour table: per warp for blocks of 8 warps or more (no block-wide wait
+  // at the start of a tile, which idles an SM that holds a single block), else
+  // one table per block written by warp 0 behind a barrier (fewer registers,
+  // and several resident blocks hide the wait)
+  static constexpr bool WARP_NB = W >= 8;
+  static constexpr int NB_TABLES = WARP_NB ? W : 1;
 };
 
 // bytes of dynamic shared memory: the double-buffered half-spinors plus, for
 // FP16 output, one float per (warp, lane) for the per-site maximum
+// (and, per warp, the 8 neighbour indices of the tile's 32 sites)
 template <int D, bool REAL, int R, int P>
 constexpr size_t rows_smem_bytes() {
   return (size_t)2 * 2 * RowsGeom<D, REAL, R>::DC * 32 * sizeof(cx<typename PT<P>::A>) +
-         (P == 2 ? (size_t)RowsGeom<D, REAL, R>::W * 32 * 4 : 0);
+         (P == 2 ? (size_t)RowsGeom<D, REAL, R>::W * 32 * 4 : 0) + (size_t)RowsGeom<D, REAL, R>::NB_TABLES * 8 * 32 * 4;
 }
 
 // r0[r] += V[a_r][c] h0[c], r1[r] += V[a_r][c] h1[c] over all colours, for
@@ -157,28 +164,37 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = mk(A(0), A(0));
 
-  const int64_t LLh = (int64_t)L * Lh;
-  int64_t nb[8];
-  {
+  // the 8 neighbour indices of this lane's site ([n][lane]) in shared memory,
+  // rather than in a per-thread array, which the runtime direction index would
+  // put in local memory.  WARP_NB: each warp fills its own table (warp barrier
+  // only); otherwise warp 0 fills the block's table behind a block barrier, and
+  // refills it for the next tile only after that tile's last barrier, by which
+  // time every warp has read its last entry.
+  int *nbs = reinterpret_cast<int *>(smem + rows_smem_bytes<D, REAL, R, P>() - (size_t)G::NB_TABLES * 8 * 32 * 4) +
+             (G::WARP_NB ? w * 8 * 32 : 0);
+  if (G::WARP_NB || w == 0) {
+    const int64_t LLh = (int64_t)L * Lh;
     const int tf = (s.t + 1 == T) ? 0 : s.t + 1, tb = (s.t == 0) ? T - 1 : s.t - 1;
-    nb[0] = ii + (int64_t)(tf - s.t) * L * LLh;
-    nb[1] = ii + (int64_t)(tb - s.t) * L * LLh;
+    nbs[0 * 32 + lane] = (int)(ii + (int64_t)(tf - s.t) * L * LLh);
+    nbs[1 * 32 + lane] = (int)(ii + (int64_t)(tb - s.t) * L * LLh);
     const int xf = (s.x + 1 == L) ? 0 : s.x + 1, xb = (s.x == 0) ? L - 1 : s.x - 1;
-    nb[2] = ii - (s.x >> 1) + (xf >> 1);
-    nb[3] = ii - (s.x >> 1) + (xb >> 1);
+    nbs[2 * 32 + lane] = (int)(ii - (s.x >> 1) + (xf >> 1));
+    nbs[3 * 32 + lane] = (int)(ii - (s.x >> 1) + (xb >> 1));
     const int yf = (s.y + 1 == L) ? 0 : s.y + 1, yb = (s.y == 0) ? L - 1 : s.y - 1;
-    nb[4] = ii + (int64_t)(yf - s.y) * Lh;
-    nb[5] = ii + (int64_t)(yb - s.y) * Lh;
+    nbs[4 * 32 + lane] = (int)(ii + (int64_t)(yf - s.y) * Lh);
+    nbs[5 * 32 + lane] = (int)(ii + (int64_t)(yb - s.y) * Lh);
     const int zf = (s.z + 1 == L) ? 0 : s.z + 1, zb = (s.z == 0) ? L - 1 : s.z - 1;
-    nb[6] = ii + (int64_t)(zf - s.z) * LLh;
-    nb[7] = ii + (int64_t)(zb - s.z) * LLh;
+    nbs[6 * 32 + lane] = (int)(ii + (int64_t)(zf - s.z) * LLh);
+    nbs[7 * 32 + lane] = (int)(ii + (int64_t)(zb - s.z) * LLh);
   }
+  if (G::WARP_NB) __syncwarp();
+  else __syncthreads();
 
 #pragma unroll 1
   for (int n = 0; n < 8; ++n) {
     const int mu = n >> 1;
     const bool bwd = n & 1;
-    const int64_t j = nb[n];
+    const int64_t j = nbs[n * 32 + lane];
     const A sig = bwd ? sg : -sg;
     const A scl = (P == 2) ? (A)isc[j] : A(1);
     cx<A> *hs = sh + (n & 1) * (2 * DC * 32);

@@ -82,6 +82,9 @@ struct hr_lattice {
   } while (0)
 
 void hr_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// library-owned large buffers: through the allocator of hr_set_allocator, else cudaMalloc
+int hr_dev_alloc(void **p, size_t bytes);
+void hr_dev_free(void *p);
 int hr_check_launch(const char *what);
 
 // ------------------------------------------------------------- geometry ----

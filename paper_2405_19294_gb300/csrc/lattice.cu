@@ -1,16 +1,94 @@
 // Lattice handle, status strings, stream handling and the canonical <->
 // internal spinor conversions (pack / unpack, including the FP16 per-site code).
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+
 #include "cplx.cuh"
+
 #include "hr_internal.h"
 
 static char g_last_error[512];
 
 void hr_note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+// ---------------------------------------------------- device allocations ----
+// Large library-owned buffers (links, clover, workspaces) go through an
+// optional caller-supplied allocator (e.g. PyTorch's caching allocator); each
+// allocation remembers the release function it came with, so changing the
+// allocator later never frees a block through the wrong one.
+namespace {
+struct AllocRec {
+  hr_free_fn fn;
+  void *ctx;
+  size_t bytes;
+};
+std::mutex g_amu;
+hr_alloc_fn g_alloc = nullptr;
+hr_free_fn g_free = nullptr;
+void *g_actx = nullptr;
+std::map<void *, AllocRec> g_arec;
+}  // namespace
+
+extern "C" int hr_set_allocator(hr_alloc_fn alloc, hr_free_fn release, void *ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return HR_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_amu);
+  g_alloc = alloc;
+  g_free = release;
+  g_actx = ctx;
+  return HR_OK;
+}
+
+int hr_dev_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  hr_alloc_fn a;
+  hr_free_fn f;
+  void *c;
+  {
+    std::lock_guard<std::mutex> lk(g_amu);
+    a = g_alloc;
+    f = g_free;
+    c = g_actx;
+  }
+  if (!a) {
+    HR_CUDA(cudaMalloc(p, bytes));
+    return HR_OK;
+  }
+  void *q = a(bytes, c);  // outside the lock: the allocator may call back into anything
+  if (!q) return HR_ERR_NOMEM;
+  if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+    f(q, bytes, c);
+    return HR_ERR_ARG;  // the library's vector loads need 256-byte alignment
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_amu);
+    g_arec[q] = AllocRec{f, c, bytes};
+  }
+  *p = q;
+  return HR_OK;
+}
+
+void hr_dev_free(void *p) {
+  if (!p) return;
+  AllocRec r;
+  bool mine = false;
+  {
+    std::lock_guard<std::mutex> lk(g_amu);
+    auto it = g_arec.find(p);
+    if (it != g_arec.end()) {
+      r = it->second;
+      g_arec.erase(it);
+      mine = true;
+    }
+  }
+  if (mine) r.fn(p, r.bytes, r.ctx);
+  else cudaFree(p);
 }
 
 int hr_check_launch(const char *what) {
@@ -102,18 +180,18 @@ void hr_cg_free(hr_lattice *lat);
 
 extern "C" int hr_lattice_destroy(hr_lattice *lat) {
   if (!lat) return HR_ERR_ARG;
-  cudaStreamSynchronize(lat->stream);
+  cudaDeviceSynchronize();  // the solver streams too: nothing may still use what is freed below
   for (int p = 0; p < 3; ++p) {
-    cudaFree(lat->links[p]);
-    cudaFree(lat->rlinks[p]);
+    hr_dev_free(lat->links[p]);
+    hr_dev_free(lat->rlinks[p]);
   }
-  for (int b = 0; b < 4; ++b) cudaFree(lat->halo[b]);
-  cudaFree(lat->clover_term);
+  for (int b = 0; b < 4; ++b) hr_dev_free(lat->halo[b]);
+  hr_dev_free(lat->clover_term);
   for (int p = 0; p < 2; ++p) {
-    cudaFree(lat->clover_A[p]);
-    cudaFree(lat->clover_Ainv[p]);
+    hr_dev_free(lat->clover_A[p]);
+    hr_dev_free(lat->clover_Ainv[p]);
   }
-  cudaFree(lat->tmp);
+  hr_dev_free(lat->tmp);
   cudaFree(lat->dev_err);
   cudaFree(lat->red_partials);
   cudaFree(lat->red_count);

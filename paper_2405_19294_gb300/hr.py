@@ -82,6 +82,7 @@ _SIGS = {
     "hr_domain_hop_end": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "hr_domains_dphi": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, C.c_double,
                                   C.c_int, C.c_int, C.c_int]),
+    "hr_set_allocator": (C.c_int, [_P, _P, _P]),
     "hr_status_string": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -265,6 +266,34 @@ class Lattice:
         return {"status": rc, "iterations": st.iterations, "outer_steps": st.outer_steps,
                 "true_residual": st.true_residual, "seconds": st.seconds,
                 "hop_launches": st.hop_launches}
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+_allocator_refs = []
+
+
+def use_torch_allocator(on: bool = True):
+    """Back libhr's large device buffers by PyTorch's caching allocator (on the
+    current device and stream), so they show in torch.cuda.memory_allocated()
+    and share its pool; on=False returns to cudaMalloc."""
+    import torch
+    if not on:
+        _check(_lib.hr_set_allocator(None, None, None), "hr_set_allocator")
+        return
+
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes)
+        except Exception:
+            return None
+
+    def release(ptr, nbytes, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = _ALLOC_FN(alloc), _FREE_FN(release)
+    _allocator_refs.append((fa, ff))   # the C side keeps the pointers: keep the thunks alive
+    _check(_lib.hr_set_allocator(C.cast(fa, _P), C.cast(ff, _P), None), "hr_set_allocator")
 
 
 def domains_dphi(lats, outs, ins, parity: int, m0: float, prec: int, nrhs: int = 1, dagger: bool = False):

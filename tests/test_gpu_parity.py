@@ -286,3 +286,28 @@ def test_every_multi_rhs_shape_is_correct(hr, N, rep, csw, prec):
         got = _gpu_apply(lat, psi, 0, m0, csw, prec, 0, nrhs=nrhs)
         for r in range(nrhs):
             assert rel_err(got[r], refs[r], mask) < TOL[prec], (sh, r)
+
+
+def test_torch_caching_allocator_backs_library_buffers(hr):
+    """hr_set_allocator: the links, rows layout and Schur intermediate come from
+    PyTorch's pool and go back to it when the lattice is destroyed."""
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    hr.use_torch_allocator(True)
+    try:
+        lat, U = gpu_lattice(hr, 8, 8, 4, "sym", 1.0, 0.0)
+        links_bytes = 2 * 4 * lat.d * lat.d * lat.Vh * (16 + 8 + 4)
+        grown = torch.cuda.memory_allocated() - before
+        assert grown >= links_bytes
+        op = oracle_operator(8, 8, 4, "sym", 1.0, -0.3, 0.0)
+        psi = inputs.gaussian_spinor(3, 8, 8, lat.d)
+        got = _gpu_apply(lat, psi, 0, -0.3, 0.0, 1, 0)[0]
+        assert rel_err(got, op.apply_schur(psi[0], 0), op.geom.parity == 0) < TOL[1]
+        del U
+        lat.close()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() - before < links_bytes // 4
+    finally:
+        hr.use_torch_allocator(False)
+    lat2, _ = gpu_lattice(hr, 4, 4, 3, "fund", 1.0, 0.0)   # back on cudaMalloc
+    lat2.close()
