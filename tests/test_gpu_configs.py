@@ -24,10 +24,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CONFIGS = {
-    "c1": dict(N=3, rep="fund", T=64, L=32, eps=1.0, m0=-0.4, csw=0.0, nrhs=1, precs=(0, 1), inner=(0, 1, 2)),
+    "c1": dict(N=3, rep="fund", T=64, L=32, eps=1.0, m0=-0.4, csw=0.0, nrhs=1, precs=(0, 1, 2), inner=(0, 1, 2)),
     "c2_adj": dict(N=2, rep="adj", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
     "c2_asym": dict(N=4, rep="asym", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
-    "c3": dict(N=3, rep="sym", T=64, L=32, eps=1.0, m0=-0.35, csw=1.0, nrhs=12, precs=(1,), inner=(1,)),
+    "c3": dict(N=3, rep="sym", T=64, L=32, eps=1.0, m0=-0.35, csw=1.0, nrhs=12, precs=(0, 1, 2), inner=(1,)),
 }
 
 _cache = {}
