@@ -327,11 +327,13 @@ static int bi_iteration(BiCtx &c) {
     else K<1><<<grid, 256, 0, c.s>>>(__VA_ARGS__);                                  \
     HR_TRY(hr_check_launch(#K));                                                    \
   } while (0)
+  // hops of right-hand sides already frozen (|r|^2 <= stop) return at once
+  const double *rr = g_bi->q + (size_t)Q_RR * BI_MAXRHS, *stop = g_bi->q + (size_t)Q_STOP * BI_MAXRHS;
   L3(bi_p_kernel, p, r, v, c.f, c.sc);
-  HR_TRY(hr_dphi_impl(c.lat, v, p, c.parity, c.m0, c.csw, c.prec, c.nrhs, 0, c.s));
+  HR_TRY(hr_dphi_impl_skip(c.lat, v, p, c.parity, c.m0, c.csw, c.prec, c.nrhs, 0, c.s, rr, stop));
   L3(bi_alpha_kernel, rh, v, c.f, c.sc);
   L3(bi_s_kernel, s, r, v, c.f, c.sc);
-  HR_TRY(hr_dphi_impl(c.lat, t, s, c.parity, c.m0, c.csw, c.prec, c.nrhs, 0, c.s));
+  HR_TRY(hr_dphi_impl_skip(c.lat, t, s, c.parity, c.m0, c.csw, c.prec, c.nrhs, 0, c.s, rr, stop));
   L3(bi_omega_kernel, t, s, c.f, c.sc);
   L3(bi_xr_kernel, x, r, p, s, t, rh, c.f, c.sc);
 #undef L3

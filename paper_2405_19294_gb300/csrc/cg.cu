@@ -90,15 +90,19 @@ struct CgCtx {
 };
 
 // Ap = M p = Dhat^+ Dhat p through t; fused |t|^2 -> pAp and alpha
+// Inside a CG chunk (rr given) the hops of right-hand sides already at their
+// stop value return at once: a chunk runs past convergence by up to
+// check_every - 1 iterations, and those cost only launches, not the stencil.
 static int apply_normal(CgCtx &c, int prec, void *Ap, const void *p, void *t, const FieldDesc &f, int finish,
                         const double *rr) {
-  HR_TRY(hr_dphi_impl(c.lat, t, p, c.parity, c.m0, c.csw, prec, c.nrhs, 0, c.s));
+  const double *stop = rr ? c.red.stop : nullptr;
+  HR_TRY(hr_dphi_impl_skip(c.lat, t, p, c.parity, c.m0, c.csw, prec, c.nrhs, 0, c.s, rr, stop));
   RedArgs red = c.red;
   red.out = S(c.lat->cg, S_PAP);
   red.rr = rr;
   red.alpha = S(c.lat->cg, S_ALPHA);
   if (finish != RED_NONE_SKIP) HR_TRY(hr_blas_norm2(f, prec, t, c.nrhs, red, finish, c.s));
-  HR_TRY(hr_dphi_impl(c.lat, Ap, t, c.parity, c.m0, c.csw, prec, c.nrhs, 1, c.s));
+  HR_TRY(hr_dphi_impl_skip(c.lat, Ap, t, c.parity, c.m0, c.csw, prec, c.nrhs, 1, c.s, rr, stop));
   return HR_OK;
 }
 

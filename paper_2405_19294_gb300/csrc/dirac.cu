@@ -430,6 +430,11 @@ static const void *clover_ptr(const hr_lattice *lat, int prec, bool inverse, int
 
 int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw, int prec, int nrhs,
                  int dagger, cudaStream_t st) {
+  return hr_dphi_impl_skip(lat, out, in, parity, m0, csw, prec, nrhs, dagger, st, nullptr, nullptr);
+}
+
+int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw, int prec,
+                      int nrhs, int dagger, cudaStream_t st, const double *skip_rr, const double *skip_stop) {
   const bool clover = csw != 0.0;
   if (clover) HR_TRY(hr_clover_prepare(lat, m0));
   const size_t fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
@@ -440,6 +445,8 @@ int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double 
   a.rlinks = lat->rlinks[prec];
   a.dagger = dagger;
   a.nrhs = nrhs;
+  a.skip_rr = skip_rr;
+  a.skip_stop = skip_stop;
   if (parity == HR_FULL) {
     // out_p = A_pp in_p - 1/2 H in_q, both parities; rhs fields are [even | odd]
     for (int p = 0; p < 2; ++p) {

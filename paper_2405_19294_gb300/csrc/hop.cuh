@@ -36,7 +36,13 @@ struct HopK {
   double sgn, coef, diag;
   const void *rlinks;  // rows-kernel link layout (rows kernel only)
   int tmask;           // time-slab bulk pass (site kernel only)
+  const double *skip_rr, *skip_stop;  // converged-rhs skip (see HopArgs)
 };
+
+// true when right-hand side rhs has converged and its hop is not needed
+__device__ __forceinline__ bool rhs_done(const HopK &k, int rhs) {
+  return k.skip_rr && k.skip_rr[rhs] <= k.skip_stop[rhs];
+}
 
 // Blocks are numbered right-hand side fastest: block b handles tile b / nrhs
 // of right-hand side b % nrhs, so the nrhs blocks that read the same links run
@@ -333,6 +339,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k) {
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
+  if (rhs_done(k, rhs)) return;
   const int64_t i = tile * blockDim.x + threadIdx.x;
   if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
 }
@@ -374,6 +381,8 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   k.diag = a.diag;
   k.nrhs = a.nrhs;
   k.tmask = a.tmask;
+  k.skip_rr = a.skip_rr;
+  k.skip_stop = a.skip_stop;
   return k;
 }
 

@@ -132,6 +132,12 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
   const int nrb = (k.nrhs + R - 1) / R;
   const int64_t tile = blockIdx.x / nrb;
   const int rhs = (int)(blockIdx.x % nrb) * R + q;
+  if (k.skip_rr) {  // the whole block returns only when every rhs it covers has converged
+    const int r0 = (int)(blockIdx.x % nrb) * R;
+    bool any = false;
+    for (int qq = 0; qq < R && r0 + qq < k.nrhs; ++qq) any |= !rhs_done(k, r0 + qq);
+    if (!any) return;
+  }
   const int64_t i0 = tile * S;
   const int64_t i = i0 + s;
   const int64_t Vh = k.Vh;

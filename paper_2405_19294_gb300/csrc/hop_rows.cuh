@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(RowsGeom<D, REAL, R>::NT) hop_rows_kernel(HopK
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
+  if (rhs_done(k, rhs)) return;  // block-uniform: before any barrier
   rows_zero_pads<D, REAL, P, R>(rows_smem);
   hop_rows_tile<D, REAL, P, R>(k, tile, rhs, rows_smem);
 }

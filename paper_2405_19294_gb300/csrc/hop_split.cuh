@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(128) hop_split_kernel(HopK k) {
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
+  if (rhs_done(k, rhs)) return;
   hop_split_tile<D, REAL, P, G>(k, tile, rhs, sh);
 }
 

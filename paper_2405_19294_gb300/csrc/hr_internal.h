@@ -136,6 +136,8 @@ struct HopArgs {
   int nrhs;
   double *norm_partials;  // optional fused |out|^2 per block (null = off)
   int tmask;              // 1: skip the t hops that cross the slab faces (sub-domain bulk pass)
+  const double *skip_rr;  // with skip_stop: a rhs whose skip_rr <= skip_stop is done, its blocks
+  const double *skip_stop;  // return at once (CG chunks past convergence); null = never skip
 };
 
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
@@ -228,6 +230,9 @@ void *hr_cg_field(hr_lattice *lat, int prec, int which);
 // dirac.cu
 int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,
                  int prec, int nrhs, int dagger, cudaStream_t s);
+// the same, with the converged-rhs skip of HopArgs (rr, stop: device arrays per rhs)
+int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw, int prec,
+                      int nrhs, int dagger, cudaStream_t st, const double *rr, const double *stop);
 int hr_ensure_tmp(hr_lattice *lat, size_t bytes);
 int hr_clover_prepare(hr_lattice *lat, double m0);
 
