@@ -268,6 +268,16 @@ __global__ void bi_xr_kernel(char *x, char *r, const char *p, const char *s, con
 }  // namespace
 
 // --------------------------------------------------------------------- driver
+// What an instantiated chunk graph depends on (lattice geometry and buffers,
+// operator parameters, launch shape): replayed only while all of it matches.
+struct BiGraphKey {
+  const void *lat, *links, *tmp, *clover;
+  int T, L, d, prec, nrhs, parity, check_every, shape;
+  const void *f;
+  size_t fb;
+  double m0, csw;
+};
+
 struct BiWork {
   size_t cap[3];
   void *f[3][8];  // per precision: x, r, rhat, p, v, s, t, spare
@@ -277,6 +287,8 @@ struct BiWork {
   int *err, *iters;
   double *host;
   cudaStream_t s;
+  cudaGraphExec_t exec[2];  // last chunk graph per inner precision (FP64, FP32)
+  BiGraphKey key[2];
 };
 
 static BiWork *g_bi = nullptr;  // one workspace per process, grown as needed (guarded by callers' serialisation)
@@ -297,6 +309,11 @@ static int bi_work(int prec, size_t bytes) {
   }
   if (g_bi->cap[prec] < bytes) {
     HR_CUDA(cudaDeviceSynchronize());
+    for (int k = 0; k < 2; ++k)  // the graphs refer to the buffers about to be replaced
+      if (g_bi->exec[k]) {
+        cudaGraphExecDestroy(g_bi->exec[k]);
+        g_bi->exec[k] = nullptr;
+      }
     for (int k = 0; k < 8; ++k) {
       hr_dev_free(g_bi->f[prec][k]);
       g_bi->f[prec][k] = nullptr;
@@ -362,25 +379,61 @@ static int bi_loop(BiCtx &c, const double *stop, int check_every, int maxit, int
     q[Q_FROZEN * BI_MAXRHS + r] = (rr <= stop[r]) ? 1.0 : 0.0;
   }
   HR_CUDA(cudaMemcpyAsync(g_bi->q, q, sizeof(double) * Q_NS * BI_MAXRHS, cudaMemcpyHostToDevice, c.s));
-  // tune the operator outside capture, then capture a chunk of iterations
-  HR_TRY(hr_dphi_impl(c.lat, F[6], F[5], c.parity, c.m0, c.csw, c.prec, nrhs, 0, c.s));
-  cudaGraph_t graph = nullptr;
+  // tune the operator outside capture (only while its shape is not known yet),
+  // then capture a chunk of iterations -- or replay the last capture of the same key
+  const int clover = c.csw != 0.0;
+  if (hr_tuned_shape(c.lat, c.prec, nrhs, clover) < 0)
+    HR_TRY(hr_dphi_impl(c.lat, F[6], F[5], c.parity, c.m0, c.csw, c.prec, nrhs, 0, c.s));
+  if (c.parity != HR_FULL)
+    HR_TRY(hr_ensure_tmp(c.lat, hr_spinor_field_bytes(c.lat->Vh, c.lat->d, c.prec) * nrhs));
+  BiGraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.lat = c.lat;
+  key.links = c.lat->links[c.prec];
+  key.tmp = c.lat->tmp;
+  key.clover = clover ? c.lat->clover_A[c.prec == HR_F64 ? 0 : 1] : nullptr;
+  key.T = c.lat->T;
+  key.L = c.lat->L;
+  key.d = c.lat->d;
+  key.prec = c.prec;
+  key.nrhs = nrhs;
+  key.parity = c.parity;
+  key.check_every = check_every;
+  key.shape = hr_tuned_shape(c.lat, c.prec, nrhs, clover);
+  key.f = F[0];
+  key.fb = c.f.fb;
+  key.m0 = c.m0;
+  key.csw = c.csw;
+  const int slot = (c.prec == HR_F64) ? 0 : 1;
   cudaGraphExec_t exec = nullptr;
-  const double hops0 = c.lat->hop_launches;
-  HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
-  int rc = HR_OK;
-  for (int k = 0; k < check_every && rc == HR_OK; ++k) rc = bi_iteration(c);
-  cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
-  const double hops_per = c.lat->hop_launches - hops0;
-  c.lat->hop_launches = hops0;
-  if (rc != HR_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
+  double hops_per = 0.0;
+  if (g_bi->exec[slot] && memcmp(&g_bi->key[slot], &key, sizeof(key)) == 0) {
+    exec = g_bi->exec[slot];
+    hops_per = 4.0 * check_every;  // two operator applications per iteration, two hops each
+  } else {
+    if (g_bi->exec[slot]) {
+      cudaGraphExecDestroy(g_bi->exec[slot]);
+      g_bi->exec[slot] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const double hops0 = c.lat->hop_launches;
+    HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+    int rc = HR_OK;
+    for (int k = 0; k < check_every && rc == HR_OK; ++k) rc = bi_iteration(c);
+    cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
+    hops_per = c.lat->hop_launches - hops0;
+    c.lat->hop_launches = hops0;
+    if (rc != HR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    HR_CUDA(ce);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HR_CUDA(ce);
+    g_bi->exec[slot] = exec;
+    g_bi->key[slot] = key;
   }
-  HR_CUDA(ce);
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  HR_CUDA(ce);
   int done = 0, status = HR_OK;
   while (done < maxit) {
     HR_CUDA(cudaGraphLaunch(exec, c.s));
@@ -405,7 +458,6 @@ static int bi_loop(BiCtx &c, const double *stop, int check_every, int maxit, int
     }
     if (all) break;
   }
-  cudaGraphExecDestroy(exec);
   *done_out = done;
   return status;
 }

@@ -28,6 +28,17 @@
 #include "blas.cuh"
 #include "hr_internal.h"
 
+// What an instantiated chunk graph depends on: replaying it is only valid for
+// the same fields, scratch, shapes and operator parameters.
+struct CgGraphKey {
+  int pr, pp, check_every, nrhs, parity, shape;
+  const void *x, *r, *p, *Ap, *t, *tmp;
+  size_t fbr, fbp;
+  int64_t Vh;
+  int nsub;
+  double m0, csw;
+};
+
 struct hr_cg_work {
   size_t cap[3];        // bytes per buffer set, per precision
   void *f[3][6];        // per precision: r, p, Ap, t, x(low), spare
@@ -35,6 +46,8 @@ struct hr_cg_work {
   double *host;         // pinned mirror
   int *iters;           // [HR_MAX_RHS]
   cudaStream_t s;
+  cudaGraphExec_t exec[2];  // the last chunk graphs (one per inner precision pair seen), reused while
+  CgGraphKey key[2];        // their key matches: capture and instantiation cost ~1 ms each
 };
 
 enum { S_RR0 = 0, S_RR1, S_PAP, S_ALPHA, S_BETA, S_STOP, S_A, S_B, S_OUT, NS };
@@ -42,6 +55,8 @@ enum { S_RR0 = 0, S_RR1, S_PAP, S_ALPHA, S_BETA, S_STOP, S_A, S_B, S_OUT, NS };
 void hr_cg_free(hr_lattice *lat) {
   hr_cg_work *w = lat->cg;
   if (!w) return;
+  for (int k = 0; k < 2; ++k)
+    if (w->exec[k]) cudaGraphExecDestroy(w->exec[k]);
   for (int p = 0; p < 3; ++p)
     for (int q = 0; q < 6; ++q) hr_dev_free(w->f[p][q]);
   cudaFree(w->scal);
@@ -65,6 +80,11 @@ static int cg_work(hr_lattice *lat, int prec, size_t bytes) {
   }
   hr_cg_work *w = lat->cg;
   if (w->cap[prec] < bytes) {
+    for (int k = 0; k < 2; ++k)  // the graphs refer to the buffers about to be replaced
+      if (w->exec[k]) {
+        cudaGraphExecDestroy(w->exec[k]);
+        w->exec[k] = nullptr;
+      }
     for (int q = 0; q < 6; ++q) {
       hr_dev_free(w->f[prec][q]);
       w->f[prec][q] = nullptr;
@@ -131,27 +151,67 @@ static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap
   hr_cg_work *w = c.lat->cg;
   if (check_every < 2) check_every = 2;
   check_every &= ~1;  // even: the rr double buffer returns to S_RR0
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // one uncaptured application first: lets the autotuner time the hop shapes
-  // (it cannot while the stream is being captured); t and Ap are scratch
-  HR_TRY(hr_dphi_impl(c.lat, t, p, c.parity, c.m0, c.csw, pp, c.nrhs, 0, c.s));
-  HR_TRY(hr_dphi_impl(c.lat, Ap, t, c.parity, c.m0, c.csw, pp, c.nrhs, 1, c.s));
-  const double hops_before = c.lat->hop_launches;  // capture records launches, replays run them
-  HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
-  int rc = HR_OK;
-  for (int k = 0; k < check_every && rc == HR_OK; ++k) rc = cg_iteration(c, pr, pp, x, r, p, Ap, t, fr, fp, k & 1);
-  cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
-  const double hops_per_replay = c.lat->hop_launches - hops_before;
-  c.lat->hop_launches = hops_before;
-  if (rc != HR_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
+  const int clover = c.csw != 0.0;
+  // an uncaptured application first when the hop shape is not tuned yet: the
+  // autotuner times candidates, which it cannot do while the stream is being
+  // captured (t and Ap are scratch)
+  if (hr_tuned_shape(c.lat, pp, c.nrhs, clover) < 0) {
+    HR_TRY(hr_dphi_impl(c.lat, t, p, c.parity, c.m0, c.csw, pp, c.nrhs, 0, c.s));
+    HR_TRY(hr_dphi_impl(c.lat, Ap, t, c.parity, c.m0, c.csw, pp, c.nrhs, 1, c.s));
   }
-  HR_CUDA(ce);
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  HR_CUDA(ce);
+  if (c.parity != HR_FULL) HR_TRY(hr_ensure_tmp(c.lat, hr_spinor_field_bytes(c.lat->Vh, c.lat->d, pp) * c.nrhs));
+  CgGraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.pr = pr;
+  key.pp = pp;
+  key.check_every = check_every;
+  key.nrhs = c.nrhs;
+  key.parity = c.parity;
+  key.shape = hr_tuned_shape(c.lat, pp, c.nrhs, clover);
+  key.x = x;
+  key.r = r;
+  key.p = p;
+  key.Ap = Ap;
+  key.t = t;
+  key.tmp = c.lat->tmp;
+  key.fbr = fr.fb;
+  key.fbp = fp.fb;
+  key.Vh = fr.Vh;
+  key.nsub = fr.nsub;
+  key.m0 = c.m0;
+  key.csw = c.csw;
+  const int slot = (pp == HR_F16) ? 1 : 0;
+  cudaGraphExec_t exec = nullptr;
+  double hops_per_replay = 0.0;
+  cudaError_t ce = cudaSuccess;
+  if (w->exec[slot] && memcmp(&w->key[slot], &key, sizeof(key)) == 0) {
+    exec = w->exec[slot];
+    hops_per_replay = 4.0 * check_every;  // two Dhat per iteration, two hops each
+  } else {
+    if (w->exec[slot]) {
+      cudaGraphExecDestroy(w->exec[slot]);
+      w->exec[slot] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const double hops_before = c.lat->hop_launches;  // capture records launches, replays run them
+    HR_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+    int rc = HR_OK;
+    for (int k = 0; k < check_every && rc == HR_OK; ++k)
+      rc = cg_iteration(c, pr, pp, x, r, p, Ap, t, fr, fp, k & 1);
+    ce = cudaStreamEndCapture(c.s, &graph);
+    hops_per_replay = c.lat->hop_launches - hops_before;
+    c.lat->hop_launches = hops_before;
+    if (rc != HR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    HR_CUDA(ce);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HR_CUDA(ce);
+    w->exec[slot] = exec;
+    w->key[slot] = key;
+  }
   int done = 0;
   int status = HR_OK;
   while (done < maxit) {
@@ -174,8 +234,10 @@ static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap
     }
     if (all) break;
   }
-  cudaGraphExecDestroy(exec);
   if (ce != cudaSuccess) {
+    // a failed replay leaves the cached graph in doubt: drop it
+    cudaGraphExecDestroy(exec);
+    w->exec[slot] = nullptr;
     hr_note_cuda_error(ce, "cg_loop", __FILE__, __LINE__);
     return HR_ERR_CUDA;
   }
