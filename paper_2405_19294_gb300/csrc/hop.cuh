@@ -36,13 +36,17 @@ struct HopK {
   double sgn, coef, diag;
   const void *rlinks;  // rows-kernel link layout (rows kernel only)
   int tmask;           // time-slab bulk pass (site kernel only)
-  const double *skip_rr, *skip_stop;  // converged-rhs skip (see HopArgs)
 };
 
+// Converged-rhs skip (see HopArgs), a kernel parameter of its own: growing
+// HopK moved the compiler's register and load scheduling of the stencils.
+struct SkipK {
+  const double *rr, *stop;
+};
+static inline SkipK make_skipk(const HopArgs &a) { return SkipK{a.skip_rr, a.skip_stop}; }
+
 // true when right-hand side rhs has converged and its hop is not needed
-__device__ __forceinline__ bool rhs_done(const HopK &k, int rhs) {
-  return k.skip_rr && k.skip_rr[rhs] <= k.skip_stop[rhs];
-}
+__device__ __forceinline__ bool rhs_done(const SkipK &sk, int rhs) { return sk.rr && sk.rr[rhs] <= sk.stop[rhs]; }
 
 // Blocks are numbered right-hand side fastest: block b handles tile b / nrhs
 // of right-hand side b % nrhs, so the nrhs blocks that read the same links run
@@ -335,11 +339,11 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 // MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
 // loads in flight per thread) and 64 x 12 (at most ~85 registers: more warps).
 template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false>
-__global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k) {
+__global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k, SkipK sk) {
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
-  if (rhs_done(k, rhs)) return;
+  if (rhs_done(sk, rhs)) return;
   const int64_t i = tile * blockDim.x + threadIdx.x;
   if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
 }
@@ -381,17 +385,15 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   k.diag = a.diag;
   k.nrhs = a.nrhs;
   k.tmask = a.tmask;
-  k.skip_rr = a.skip_rr;
-  k.skip_stop = a.skip_stop;
   return k;
 }
 
 template <int D, bool REAL, int P>
-static void launch_site(const HopK &k, dim3 grid, int bs, int variant, cudaStream_t st) {
-  if (k.tmask) hop_kernel<D, REAL, P, 256, 1, true><<<grid, bs, 0, st>>>(k);  // time-slab bulk pass
-  else if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k);
-  else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k);
-  else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k);
+static void launch_site(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st) {
+  if (k.tmask) hop_kernel<D, REAL, P, 256, 1, true><<<grid, bs, 0, st>>>(k, sk);  // time-slab bulk pass
+  else if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k, sk);
+  else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k, sk);
+  else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k, sk);
 }
 
 // Launch the site-per-thread kernel for (D, REAL) of precision P with `bs`
@@ -399,23 +401,24 @@ static void launch_site(const HopK &k, dim3 grid, int bs, int variant, cudaStrea
 template <int P>
 int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int bs, int variant) {
   const HopK k = make_hopk(lat, a);
+  const SkipK sk = make_skipk(a);
   dim3 grid((unsigned)(((lat->Vh + bs - 1) / bs) * a.nrhs));
   const int d = lat->d;
   if (lat->is_real) {
     switch (d) {
-      case 3: launch_site<3, true, P>(k, grid, bs, variant, st); break;
-      case 8: launch_site<8, true, P>(k, grid, bs, variant, st); break;
+      case 3: launch_site<3, true, P>(k, sk, grid, bs, variant, st); break;
+      case 8: launch_site<8, true, P>(k, sk, grid, bs, variant, st); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   } else {
     switch (d) {
-      case 2: launch_site<2, false, P>(k, grid, bs, variant, st); break;
-      case 3: launch_site<3, false, P>(k, grid, bs, variant, st); break;
-      case 4: launch_site<4, false, P>(k, grid, bs, variant, st); break;
-      case 5: launch_site<5, false, P>(k, grid, bs, variant, st); break;
-      case 6: launch_site<6, false, P>(k, grid, bs, variant, st); break;
-      case 7: launch_site<7, false, P>(k, grid, bs, variant, st); break;
-      case 8: launch_site<8, false, P>(k, grid, bs, variant, st); break;
+      case 2: launch_site<2, false, P>(k, sk, grid, bs, variant, st); break;
+      case 3: launch_site<3, false, P>(k, sk, grid, bs, variant, st); break;
+      case 4: launch_site<4, false, P>(k, sk, grid, bs, variant, st); break;
+      case 5: launch_site<5, false, P>(k, sk, grid, bs, variant, st); break;
+      case 6: launch_site<6, false, P>(k, sk, grid, bs, variant, st); break;
+      case 7: launch_site<7, false, P>(k, sk, grid, bs, variant, st); break;
+      case 8: launch_site<8, false, P>(k, sk, grid, bs, variant, st); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   }

@@ -16,7 +16,7 @@ int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, H
   const int g = sh.split_g;
   const bool real = lat->is_real != 0;
 #define HR_SPLIT_CASE(DD, RE, GG) \
-  if (d == DD && real == RE && g == GG) return launch_split<DD, RE, 0, GG>(k, a.nrhs, s);
+  if (d == DD && real == RE && g == GG) return launch_split<DD, RE, 0, GG>(k, make_skipk(a), a.nrhs, s);
   HR_SPLIT_SHAPES(HR_SPLIT_CASE)
 #undef HR_SPLIT_CASE
   return HR_ERR_UNSUPPORTED;

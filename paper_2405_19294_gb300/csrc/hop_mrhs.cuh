@@ -119,7 +119,7 @@ __device__ __forceinline__ void clover_apply_staged(const char *cl, int s, cx<ty
 }
 
 template <int D, bool REAL, int P, int S, bool CLOVER>
-__global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
+__global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, SkipK sk, int R) {
   typedef typename PT<P>::A A;
   constexpr int NCH = REAL ? (D * D + 1) / 2 : D * D;  // link chunks
   constexpr int ES = (P == 0) ? 16 : (P == 1 ? 8 : 4);  // bytes per link chunk
@@ -132,10 +132,10 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
   const int nrb = (k.nrhs + R - 1) / R;
   const int64_t tile = blockIdx.x / nrb;
   const int rhs = (int)(blockIdx.x % nrb) * R + q;
-  if (k.skip_rr) {  // the whole block returns only when every rhs it covers has converged
+  if (sk.rr) {  // the whole block returns only when every rhs it covers has converged
     const int r0 = (int)(blockIdx.x % nrb) * R;
     bool any = false;
-    for (int qq = 0; qq < R && r0 + qq < k.nrhs; ++qq) any |= !rhs_done(k, r0 + qq);
+    for (int qq = 0; qq < R && r0 + qq < k.nrhs; ++qq) any |= !rhs_done(sk, r0 + qq);
     if (!any) return;
   }
   const int64_t i0 = tile * S;
@@ -289,38 +289,39 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, int R) {
 }
 
 template <int D, bool REAL, int P, int S>
-int launch_mrhs_t(const HopK &k, cudaStream_t st) {
+int launch_mrhs_t(const HopK &k, SkipK sk, cudaStream_t st) {
   const int R = (k.nrhs < 256 / S) ? k.nrhs : 256 / S;
   const int nrb = (k.nrhs + R - 1) / R;
   const int64_t tiles = (k.Vh + S - 1) / S;
-  if (k.clover) hop_mrhs_kernel<D, REAL, P, S, true><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, R);
-  else hop_mrhs_kernel<D, REAL, P, S, false><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, R);
+  if (k.clover) hop_mrhs_kernel<D, REAL, P, S, true><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, sk, R);
+  else hop_mrhs_kernel<D, REAL, P, S, false><<<(unsigned)(tiles * nrb), S * R, 0, st>>>(k, sk, R);
   return hr_check_launch("hop_mrhs_kernel");
 }
 
 // S sites per block: 16 (8 for FP64, whose chunks are twice as large), and
 // half that for d_R = 8, whose staged links and clover blocks are larger.
 template <int D, bool REAL, int P>
-int mrhs_pick(const HopK &k, cudaStream_t st, int S) {
+int mrhs_pick(const HopK &k, SkipK sk, cudaStream_t st, int S) {
   constexpr int SMAX = (D == 8) ? (P == 0 ? 4 : 8) : (P == 0 ? 8 : 16);
-  if (S >= SMAX) return launch_mrhs_t<D, REAL, P, SMAX>(k, st);
-  return launch_mrhs_t<D, REAL, P, (SMAX >= 8 ? SMAX / 2 : SMAX)>(k, st);
+  if (S >= SMAX) return launch_mrhs_t<D, REAL, P, SMAX>(k, sk, st);
+  return launch_mrhs_t<D, REAL, P, (SMAX >= 8 ? SMAX / 2 : SMAX)>(k, sk, st);
 }
 
 // Multi-rhs launch for the one-site-per-thread classes (d_R <= 8).
 template <int P>
 int hop_mrhs_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int S) {
   const HopK k = make_hopk(lat, a);
+  const SkipK sk = make_skipk(a);
   const int d = lat->d;
   if (lat->is_real) {
-    if (d == 3) return mrhs_pick<3, true, P>(k, st, S);
-    if (d == 8) return mrhs_pick<8, true, P>(k, st, S);
+    if (d == 3) return mrhs_pick<3, true, P>(k, sk, st, S);
+    if (d == 8) return mrhs_pick<8, true, P>(k, sk, st, S);
   } else {
-    if (d == 2) return mrhs_pick<2, false, P>(k, st, S);
-    if (d == 3) return mrhs_pick<3, false, P>(k, st, S);
-    if (d == 4) return mrhs_pick<4, false, P>(k, st, S);
-    if (d == 5) return mrhs_pick<5, false, P>(k, st, S);
-    if (d == 6) return mrhs_pick<6, false, P>(k, st, S);
+    if (d == 2) return mrhs_pick<2, false, P>(k, sk, st, S);
+    if (d == 3) return mrhs_pick<3, false, P>(k, sk, st, S);
+    if (d == 4) return mrhs_pick<4, false, P>(k, sk, st, S);
+    if (d == 5) return mrhs_pick<5, false, P>(k, sk, st, S);
+    if (d == 6) return mrhs_pick<6, false, P>(k, sk, st, S);
   }
   return HR_ERR_UNSUPPORTED;
 }

@@ -300,12 +300,12 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
 }
 
 template <int D, bool REAL, int P, int R>
-__global__ void __launch_bounds__(RowsGeom<D, REAL, R>::NT) hop_rows_kernel(HopK k) {
+__global__ void __launch_bounds__(RowsGeom<D, REAL, R>::NT) hop_rows_kernel(HopK k, SkipK sk) {
   extern __shared__ __align__(16) unsigned char rows_smem[];
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
-  if (rhs_done(k, rhs)) return;  // block-uniform: before any barrier
+  if (rhs_done(sk, rhs)) return;  // block-uniform: before any barrier
   rows_zero_pads<D, REAL, P, R>(rows_smem);
   hop_rows_tile<D, REAL, P, R>(k, tile, rhs, rows_smem);
 }
@@ -338,12 +338,12 @@ static int rows_smem_optin(F *fn, size_t bytes) {
 }
 
 template <int D, bool REAL, int P, int R>
-int launch_rows(const HopK &k, int nrhs, cudaStream_t st) {
+int launch_rows(const HopK &k, SkipK sk, int nrhs, cudaStream_t st) {
   constexpr size_t sm = rows_smem_bytes<D, REAL, R, P>();
   static int opt = rows_smem_optin(hop_rows_kernel<D, REAL, P, R>, sm);
   if (opt != HR_OK) return opt;
   dim3 grid((unsigned)(((k.Vh + 31) / 32) * nrhs));
-  hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, REAL, R>::NT, sm, st>>>(k);
+  hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, REAL, R>::NT, sm, st>>>(k, sk);
   return hr_check_launch("hop_rows_kernel");
 }
 
@@ -352,10 +352,11 @@ int rows_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int r
   if (a.clover) return HR_ERR_UNSUPPORTED;
   if (!a.rlinks) return HR_ERR_STATE;
   const HopK k = make_hopk(lat, a);
+  const SkipK sk = make_skipk(a);
   const int d = lat->d;
   const bool real = lat->is_real != 0;
 #define HR_ROWS_CASE(DD, RE, RR) \
-  if (d == DD && real == RE && rows == RR) return launch_rows<DD, RE, P, RR>(k, a.nrhs, s);
+  if (d == DD && real == RE && rows == RR) return launch_rows<DD, RE, P, RR>(k, sk, a.nrhs, s);
   HR_ROWS_SHAPES(HR_ROWS_CASE)
 #undef HR_ROWS_CASE
   return HR_ERR_UNSUPPORTED;

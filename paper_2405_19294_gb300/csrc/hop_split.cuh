@@ -203,12 +203,12 @@ __device__ __forceinline__ void hop_split_tile(const HopK &k, int64_t tile, int 
 }
 
 template <int D, bool REAL, int P, int G>
-__global__ void __launch_bounds__(128) hop_split_kernel(HopK k) {
+__global__ void __launch_bounds__(128) hop_split_kernel(HopK k, SkipK sk) {
   __shared__ cx<typename PT<P>::A> sh[2][128 / G][2 * D];  // half-spinor per site, double buffered
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
-  if (rhs_done(k, rhs)) return;
+  if (rhs_done(sk, rhs)) return;
   hop_split_tile<D, REAL, P, G>(k, tile, rhs, sh);
 }
 
@@ -227,10 +227,10 @@ __global__ void __launch_bounds__(128) hop_split_multi_kernel(const HopK *descs,
 }
 
 template <int D, bool REAL, int P, int G>
-int launch_split(const HopK &k, int nrhs, cudaStream_t st) {
+int launch_split(const HopK &k, SkipK sk, int nrhs, cudaStream_t st) {
   constexpr int SPB = 128 / G;
   dim3 grid((unsigned)(((k.Vh + SPB - 1) / SPB) * nrhs));
-  hop_split_kernel<D, REAL, P, G><<<grid, 128, 0, st>>>(k);
+  hop_split_kernel<D, REAL, P, G><<<grid, 128, 0, st>>>(k, sk);
   return hr_check_launch("hop_split_kernel");
 }
 
