@@ -269,7 +269,7 @@ def test_pack_unpack_direct_from_pinned_host(hr, prec):
 
 
 @pytest.mark.parametrize("N,rep,csw", [(3, "fund", 0.0), (3, "sym", 1.0), (2, "adj", 0.0), (3, "adj", 1.0),
-                                       (6, "adj", 0.0)])
+                                       (6, "adj", 0.0), (5, "fund", 1.0), (3, "fund", 1.0)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_every_multi_rhs_shape_is_correct(hr, N, rep, csw, prec):
     """Several right-hand sides at once, every candidate shape (incl. the link-staging kernel)."""
