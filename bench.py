@@ -369,20 +369,26 @@ def _suite_large_d(hr, inputs, torch):
 
 
 def run_one_dhat(spec):
-    """A single pinned-shape Dhat case for ncu captures: three applications, no timing."""
+    """A single pinned-shape Dhat case for ncu captures: three applications, no timing.
+
+    spec = N,REP,T,L,PREC,SHAPE[,CSW[,NRHS]] (defaults csw 0, one right-hand side)."""
     import torch
     from paper_2405_19294_gb300 import hr, inputs
-    N, rep, T, L, prec, shape = spec.split(",")
+    parts = spec.split(",")
+    N, rep, T, L, prec, shape = parts[:6]
+    csw = float(parts[6]) if len(parts) > 6 else 0.0
+    nrhs = int(parts[7]) if len(parts) > 7 else 1
     N, T, L = int(N), int(T), int(L)
     prec = {"f64": hr.F64, "f32": hr.F32, "f16": hr.F16}[prec]
-    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
-    fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
-    fo = lat.new_field(0, prec)
-    lat.set_shape(prec, tuple(int(v) for v in shape.split(":")))
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, csw)
+    fi = _pack_rhs(lat, inputs, torch, 1, T, L, nrhs, prec)
+    fo = lat.new_field(0, prec, nrhs)
+    lat.set_shape(prec, tuple(int(v) for v in shape.split(":")), nrhs=nrhs, clover=csw != 0)
+    m0 = -0.35 if csw else -0.4
     for _ in range(3):
-        lat.dphi(fo, fi, 0, -0.4, 0.0, prec)
+        lat.dphi(fo, fi, 0, m0, csw, prec, nrhs)
     torch.cuda.synchronize()
-    print(json.dumps({"one_dhat": spec, "d": lat.d, "shape": lat.tuned_shape(prec)}))
+    print(json.dumps({"one_dhat": spec, "d": lat.d, "shape": lat.tuned_shape(prec, nrhs=nrhs, clover=csw != 0)}))
 
 
 def _large_nc_geometry(N, target_bytes):
@@ -583,9 +589,10 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
     ap.add_argument("--T", type=int, default=WORKLOAD["T"], help="time extent (profiling runs only)")
     ap.add_argument("--L", type=int, default=WORKLOAD["L"], help="space extent (profiling runs only)")
-    ap.add_argument("--one-dhat", default="", metavar="N,REP,T,L,PREC,SHAPE",
+    ap.add_argument("--one-dhat", default="", metavar="N,REP,T,L,PREC,SHAPE[,CSW[,NRHS]]",
                     help="profiling case: build one lattice (PREC f64/f32/f16), pin the launch shape "
-                         "SHAPE = G:block:regs:mrhs:rows and apply Dhat three times, nothing else")
+                         "SHAPE = G:block:regs:mrhs:rows and apply Dhat (clover coefficient CSW, NRHS "
+                         "right-hand sides) three times, nothing else")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -83,34 +83,42 @@ __device__ __forceinline__ void hop_dir_staged(cx<typename PT<P>::A> acc[D][4], 
   }
 }
 
-// B acc for the packed Hermitian chiral blocks staged as [chunk][S] (FP64
-// chunks for FP64 fields, FP32 otherwise)
+// w = B_b v for chiral block b of the packed Hermitian blocks staged as
+// [chunk][S] (FP64 chunks for FP64 fields, FP32 otherwise); v[sp * D + c] is
+// spin 2b + sp, colour c
+template <int D, int P, int S>
+__device__ __forceinline__ void clover_block_staged(const char *cl, int s, int b, const cx<typename PT<P>::A> v[2 * D],
+                                                    cx<typename PT<P>::A> w[2 * D]) {
+  constexpr int PC = (P == 0) ? 0 : 1;
+  const int off = b * 2 * D * D;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const auto dg = sm2<PC, S>(cl, off + q, s);
+    w[2 * q] = scale(dg.x, v[2 * q]);
+    w[2 * q + 1] = scale(dg.y, v[2 * q + 1]);
+  }
+#pragma unroll
+  for (int r = 1; r < 2 * D; ++r)
+#pragma unroll
+    for (int c = 0; c < r; ++c) {
+      const auto a = sm2<PC, S>(cl, off + D + r * (r - 1) / 2 + c, s);
+      w[r] = cfma(a, v[c], w[r]);
+      w[c] = cfmac(a, v[r], w[c]);
+    }
+}
+
+// acc <- B acc, one chiral block at a time
 template <int D, int P, int S>
 __device__ __forceinline__ void clover_apply_staged(const char *cl, int s, cx<typename PT<P>::A> acc[D][4]) {
   typedef typename PT<P>::A A;
-  constexpr int PC = (P == 0) ? 0 : 1;
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
-    const int off = b * 2 * D * D;
     cx<A> v[2 * D], w[2 * D];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
       for (int c = 0; c < D; ++c) v[sp * D + c] = acc[c][2 * b + sp];
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      const cx<A> dg = sm2<PC, S>(cl, off + q, s);
-      w[2 * q] = scale(dg.x, v[2 * q]);
-      w[2 * q + 1] = scale(dg.y, v[2 * q + 1]);
-    }
-#pragma unroll
-    for (int r = 1; r < 2 * D; ++r)
-#pragma unroll
-      for (int c = 0; c < r; ++c) {
-        const cx<A> a = sm2<PC, S>(cl, off + D + r * (r - 1) / 2 + c, s);
-        w[r] = cfma(a, v[c], w[r]);
-        w[c] = cfmac(a, v[r], w[c]);
-      }
+    clover_block_staged<D, P, S>(cl, s, b, v, w);
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
@@ -118,8 +126,36 @@ __device__ __forceinline__ void clover_apply_staged(const char *cl, int s, cx<ty
   }
 }
 
+// spins 2b, 2b+1 of colour c of site i of a spinor field
+template <int P>
+__device__ __forceinline__ void ld_half_colour(const void *f, int64_t Vh, int64_t i, int c, int b,
+                                               cx<typename PT<P>::A> psi[2]) {
+  if constexpr (P == 0) {
+    const double2 *p = reinterpret_cast<const double2 *>(f);
+    const double2 v0 = __ldg(p + (int64_t)(4 * c + 2 * b) * Vh + i);
+    const double2 v1 = __ldg(p + (int64_t)(4 * c + 2 * b + 1) * Vh + i);
+    psi[0] = mk(v0.x, v0.y);
+    psi[1] = mk(v1.x, v1.y);
+  } else if constexpr (P == 1) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(f) + (int64_t)(2 * c + b) * Vh + i);
+    psi[0] = mk(a.x, a.y);
+    psi[1] = mk(a.z, a.w);
+  } else {
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(f) + ((int64_t)c * Vh + i) * 2 + b);
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    psi[0] = mk(f0.x, f0.y);
+    psi[1] = mk(f1.x, f1.y);
+  }
+}
+
+// FP32 / FP16 kernels of d_R = 6 are held to 128 registers (two 256-thread
+// blocks' worth per SM), which their clover epilogue otherwise exceeds
+template <int D, int P>
+constexpr int mrhs_min_blocks() { return (P != 0 && D == 6) ? 2 : 0; }
+
 template <int D, bool REAL, int P, int S, bool CLOVER>
-__global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, SkipK sk, int R) {
+__global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(HopK k, SkipK sk, int R) {
   typedef typename PT<P>::A A;
   constexpr int NCH = REAL ? (D * D + 1) / 2 : D * D;  // link chunks
   constexpr int ES = (P == 0) ? 16 : (P == 1 ? 8 : 4);  // bytes per link chunk
@@ -242,26 +278,34 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(HopK k, SkipK sk, int R) 
   } else {
     const void *self = reinterpret_cast<const char *>(k.self) + roff;
     const A ssc = (P == 2) ? (A)f16_scales(self, Vh, D)[i] : A(1);
-    cx<A> sv[D][4];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      ld_colour<P>(self, Vh, i, c, sv[c]);
-      if (P == 2)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) sv[c][r] = scale(ssc, sv[c][r]);
-    }
     if (CLOVER) {
-      clover_apply_staged<D, P, S>(cbuf, s, sv);
+      // acc += A self, chiral block by block (the self field is read in halves so
+      // that only one block's input and output are live next to acc)
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+      for (int b = 0; b < 2; ++b) {
+        cx<A> v[2 * D], w[2 * D];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[c][r] = acc[c][r] + sv[c][r];
+        for (int c = 0; c < D; ++c) {
+          cx<A> h[2];
+          ld_half_colour<P>(self, Vh, i, c, b, h);
+          v[c] = (P == 2) ? scale(ssc, h[0]) : h[0];
+          v[D + c] = (P == 2) ? scale(ssc, h[1]) : h[1];
+        }
+        clover_block_staged<D, P, S>(cbuf, s, b, v, w);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[c][2 * b + sp] = acc[c][2 * b + sp] + w[sp * D + c];
+      }
     } else {
       const A dg = (A)k.diag;
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+      for (int c = 0; c < D; ++c) {
+        cx<A> sv[4];
+        ld_colour<P>(self, Vh, i, c, sv);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[c][r] = axpy_r(dg, sv[c][r], acc[c][r]);
+        for (int r = 0; r < 4; ++r) acc[c][r] = axpy_r(dg, (P == 2) ? scale(ssc, sv[r]) : sv[r], acc[c][r]);
+      }
     }
   }
   if (P == 0) {
