@@ -5,9 +5,12 @@
 // site t % S, rhs t / S, so each warp reads runs of consecutive sites of one
 // rhs -- coalesced).  The links are staged in shared memory as raw storage
 // chunks ([chunk][site], conflict-free) by asynchronous copies (cp.async),
-// double-buffered by direction: while the block computes direction mu from
-// one buffer, the forward and backward links of direction mu+1 (and, during
-// the last direction, the clover blocks of the epilogue) stream into the other.
+// in a ring of three buffers by direction: while the block computes direction
+// mu from one buffer, the forward and backward links of direction mu+1 (and,
+// during the last direction, the clover blocks of the epilogue) stream into
+// the next.  With three buffers the one being refilled was last read two
+// directions earlier, before the barrier every thread passed at the start of
+// the previous direction, so one barrier per direction suffices.
 // Link and clover traffic from L2 / HBM therefore drops by R compared with
 // running the right-hand sides as separate blocks, and the staging latency
 // hides behind the arithmetic.  The arithmetic per (site, rhs) is the
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
   constexpr int ES = (P == 0) ? 16 : (P == 1 ? 8 : 4);  // bytes per link chunk
   constexpr int CES = (P == 0) ? 16 : 8;                // bytes per clover chunk
   constexpr int CCH = CLOVER ? 4 * D * D : 1;           // clover chunks per site (both blocks)
-  __shared__ __align__(16) char lbuf[2][2][NCH * S * ES];  // [buffer][forward/backward]
+  __shared__ __align__(16) char lbuf[3][2][NCH * S * ES];  // [buffer][forward/backward]
   __shared__ __align__(16) char cbuf[CCH * S * CES];
   __shared__ int64_t nbi[8][S];
   const int s = threadIdx.x % S, q = threadIdx.x / S;
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
   cp_async_commit();
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    if (mu < 3) stage_links(mu + 1, (mu + 1) & 1);
+    if (mu < 3) stage_links(mu + 1, (mu + 1) % 3);
     else stage_clover();
     cp_async_commit();
     cp_async_wait<1>();  // all but the group just issued: direction mu is in
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
     if (active) {
       const int64_t jf = nbi[2 * mu][s], jb = nbi[2 * mu + 1][s];
       const A sf = (P == 2) ? (A)isc[jf] : A(1), sb = (P == 2) ? (A)isc[jb] : A(1);
-      const char *uf = lbuf[mu & 1][0], *ub = lbuf[mu & 1][1];
+      const char *uf = lbuf[mu % 3][0], *ub = lbuf[mu % 3][1];
       switch (mu) {
         case 0:
           hop_dir_staged<D, REAL, P, 0, false, S>(acc, in, Vh, jf, uf, s, -sg, sf);
@@ -262,7 +265,6 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
           break;
       }
     }
-    __syncthreads();  // buffer mu & 1 is refilled two directions later
   }
   cp_async_wait<0>();
   __syncthreads();
