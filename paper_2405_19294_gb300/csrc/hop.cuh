@@ -115,6 +115,124 @@ __device__ __forceinline__ void reconstruct_w(R sig, R w, cx<R> r0, cx<R> r1, cx
   }
 }
 
+// ---- FP16 fields: half2 projection, mixed-precision FMAs ----
+// The projected half-spinor is formed in half2 arithmetic straight from the
+// stored FP16 components (the +-1 and +-i factors are exact; the one add rounds
+// to FP16), and the link products use fma.rn.f32.f16: both factors FP16, the
+// product and the accumulation in FP32.  Neither the spinor nor the link
+// entries pass through conversions to FP32.
+__device__ __forceinline__ float fma_f16(unsigned a, unsigned b, float c, bool hi_a, bool hi_b) {
+  const unsigned short ah = (unsigned short)(hi_a ? (a >> 16) : (a & 0xffffu));
+  const unsigned short bh = (unsigned short)(hi_b ? (b >> 16) : (b & 0xffffu));
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(ah), "h"(bh), "f"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned h2u(__half2 h) { return *reinterpret_cast<unsigned *>(&h); }
+__device__ __forceinline__ __half2 u2h(unsigned u) { return *reinterpret_cast<__half2 *>(&u); }
+// a + s b and a + i s b on half2 complex numbers; s2 = (s, s), si2 = (-s, s)
+__device__ __forceinline__ unsigned h2_axpy_r(__half2 s2, unsigned b, unsigned a) {
+  return h2u(__hfma2(s2, u2h(b), u2h(a)));
+}
+__device__ __forceinline__ unsigned h2_axpy_i(__half2 si2, unsigned b, unsigned a) {
+  return h2u(__hfma2(si2, __lowhigh2highlow(u2h(b)), u2h(a)));
+}
+// acc + u h (ADJ: conj(u) h) with u, h FP16 complex and hr = i h (ADJ: -i h)
+__device__ __forceinline__ cx<float> cfma_f16(unsigned u, unsigned h, unsigned hr, cx<float> acc) {
+  acc.x = fma_f16(u, h, acc.x, false, false);
+  acc.x = fma_f16(u, hr, acc.x, true, false);
+  acc.y = fma_f16(u, h, acc.y, false, true);
+  acc.y = fma_f16(u, hr, acc.y, true, true);
+  return acc;
+}
+
+template <int D, int MU, bool ADJ>
+__device__ __forceinline__ void hop_dir_f16(cx<float> acc[D][4], const void *in, int64_t Vh, int64_t j,
+                                            const void *lk, int64_t li, float sig, float scl) {
+  const __half2 m_r = __float2half2_rn(-sig), p_r = __float2half2_rn(sig);
+  const __half2 m_i = __floats2half2_rn(sig, -sig), p_i = __floats2half2_rn(-sig, sig);
+  // i h = (-h.y, h.x); -i h = (h.y, -h.x)
+  const __half2 rot = ADJ ? __floats2half2_rn(1.f, -1.f) : __floats2half2_rn(-1.f, 1.f);
+  unsigned h0[D], h1[D], g0[D], g1[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j);
+    if (MU == 0) {
+      h0[c] = h2_axpy_r(m_r, v.z, v.x);
+      h1[c] = h2_axpy_r(m_r, v.w, v.y);
+    } else if (MU == 1) {
+      h0[c] = h2_axpy_i(m_i, v.w, v.x);
+      h1[c] = h2_axpy_i(m_i, v.z, v.y);
+    } else if (MU == 2) {
+      h0[c] = h2_axpy_r(m_r, v.w, v.x);
+      h1[c] = h2_axpy_r(p_r, v.z, v.y);
+    } else {
+      h0[c] = h2_axpy_i(m_i, v.z, v.x);
+      h1[c] = h2_axpy_i(p_i, v.w, v.y);
+    }
+    g0[c] = h2u(__hmul2(rot, __lowhigh2highlow(u2h(h0[c]))));
+    g1[c] = h2u(__hmul2(rot, __lowhigh2highlow(u2h(h1[c]))));
+  }
+  const unsigned *lu = reinterpret_cast<const unsigned *>(lk);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<float> r0 = mk(0.f, 0.f), r1 = mk(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const unsigned u = __ldg(lu + (int64_t)(ADJ ? (c * D + a) : (a * D + c)) * Vh + li);
+      r0 = cfma_f16(u, h0[c], g0[c], r0);
+      r1 = cfma_f16(u, h1[c], g1[c], r1);
+    }
+    reconstruct_w<MU>(sig, scl, r0, r1, acc[a]);
+  }
+}
+
+// the same for real (adjoint) links: entry e of the d x d matrix is half
+// (e & 1) of 2-real chunk e >> 1; U^T for the backward hop
+template <int D, int MU, bool ADJ>
+__device__ __forceinline__ void hop_dir_f16_real(cx<float> acc[D][4], const void *in, int64_t Vh, int64_t j,
+                                                 const void *lk, int64_t li, float sig, float scl) {
+  constexpr int NC = (D * D + 1) / 2;
+  const __half2 m_r = __float2half2_rn(-sig), p_r = __float2half2_rn(sig);
+  const __half2 m_i = __floats2half2_rn(sig, -sig), p_i = __floats2half2_rn(-sig, sig);
+  unsigned h0[D], h1[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j);
+    if (MU == 0) {
+      h0[c] = h2_axpy_r(m_r, v.z, v.x);
+      h1[c] = h2_axpy_r(m_r, v.w, v.y);
+    } else if (MU == 1) {
+      h0[c] = h2_axpy_i(m_i, v.w, v.x);
+      h1[c] = h2_axpy_i(m_i, v.z, v.y);
+    } else if (MU == 2) {
+      h0[c] = h2_axpy_r(m_r, v.w, v.x);
+      h1[c] = h2_axpy_r(p_r, v.z, v.y);
+    } else {
+      h0[c] = h2_axpy_i(m_i, v.z, v.x);
+      h1[c] = h2_axpy_i(p_i, v.w, v.y);
+    }
+  }
+  const unsigned *lu = reinterpret_cast<const unsigned *>(lk);
+  unsigned u[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) u[k] = __ldg(lu + (int64_t)k * Vh + li);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<float> r0 = mk(0.f, 0.f), r1 = mk(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const int e = ADJ ? (c * D + a) : (a * D + c);
+      const bool hi = (e & 1) != 0;
+      r0.x = fma_f16(u[e >> 1], h0[c], r0.x, hi, false);
+      r0.y = fma_f16(u[e >> 1], h0[c], r0.y, hi, true);
+      r1.x = fma_f16(u[e >> 1], h1[c], r1.x, hi, false);
+      r1.y = fma_f16(u[e >> 1], h1[c], r1.y, hi, true);
+    }
+    reconstruct_w<MU>(sig, scl, r0, r1, acc[a]);
+  }
+}
+
 // One direction, one side: project psi(j), multiply by U (or U^+ when ADJ),
 // accumulate.  `lk` points at chunk 0 of the link slot, `li` is the link's
 // site index in that slot.
@@ -123,6 +241,15 @@ __device__ __forceinline__ void hop_dir(cx<typename PT<P>::A> acc[D][4], const v
                                         int64_t j, const void *lk, int64_t li,
                                         typename PT<P>::A sig, typename PT<P>::A scl) {
   typedef typename PT<P>::A A;
+  // FP16: half2 projection and mixed-precision FMAs, except for complex d_R = 5
+  // and 7, where the extra live half-spinor copies made the kernel spill and run
+  // 3-6 % slower than converting to FP32 first (d_R = 2, 3, 6 and the real
+  // classes gained 5-12 %)
+  if constexpr (P == 2 && (REAL || (D != 5 && D != 7))) {
+    if constexpr (REAL) hop_dir_f16_real<D, MU, ADJ>(acc, in, Vh, j, lk, li, sig, scl);
+    else hop_dir_f16<D, MU, ADJ>(acc, in, Vh, j, lk, li, sig, scl);
+    return;
+  }
   // FP16: the neighbour's site scale scl is applied in the reconstruction
   cx<A> h0[D], h1[D];
 #pragma unroll
