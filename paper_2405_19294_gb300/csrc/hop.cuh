@@ -146,32 +146,42 @@ __device__ __forceinline__ cx<float> cfma_f16(unsigned u, unsigned h, unsigned h
   return acc;
 }
 
+// half-spinor rows h0, h1 of the projection (1 -+ gamma_mu) of one colour's
+// stored FP16 components v = (psi0, psi1, psi2, psi3), as half2 complex numbers
+template <int MU>
+__device__ __forceinline__ void project_h2(float sig, const uint4 &v, unsigned &h0, unsigned &h1) {
+  if (MU == 0) {
+    const __half2 m_r = __float2half2_rn(-sig);
+    h0 = h2_axpy_r(m_r, v.z, v.x);
+    h1 = h2_axpy_r(m_r, v.w, v.y);
+  } else if (MU == 1) {
+    const __half2 m_i = __floats2half2_rn(sig, -sig);
+    h0 = h2_axpy_i(m_i, v.w, v.x);
+    h1 = h2_axpy_i(m_i, v.z, v.y);
+  } else if (MU == 2) {
+    h0 = h2_axpy_r(__float2half2_rn(-sig), v.w, v.x);
+    h1 = h2_axpy_r(__float2half2_rn(sig), v.z, v.y);
+  } else {
+    h0 = h2_axpy_i(__floats2half2_rn(sig, -sig), v.z, v.x);
+    h1 = h2_axpy_i(__floats2half2_rn(-sig, sig), v.w, v.y);
+  }
+}
+// i h = (-h.y, h.x), or -i h = (h.y, -h.x) when NEG
+template <bool NEG>
+__device__ __forceinline__ unsigned rot_h2(unsigned h) {
+  const __half2 rot = NEG ? __floats2half2_rn(1.f, -1.f) : __floats2half2_rn(-1.f, 1.f);
+  return h2u(__hmul2(rot, __lowhigh2highlow(u2h(h))));
+}
+
 template <int D, int MU, bool ADJ>
 __device__ __forceinline__ void hop_dir_f16(cx<float> acc[D][4], const void *in, int64_t Vh, int64_t j,
                                             const void *lk, int64_t li, float sig, float scl) {
-  const __half2 m_r = __float2half2_rn(-sig), p_r = __float2half2_rn(sig);
-  const __half2 m_i = __floats2half2_rn(sig, -sig), p_i = __floats2half2_rn(-sig, sig);
-  // i h = (-h.y, h.x); -i h = (h.y, -h.x)
-  const __half2 rot = ADJ ? __floats2half2_rn(1.f, -1.f) : __floats2half2_rn(-1.f, 1.f);
   unsigned h0[D], h1[D], g0[D], g1[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j);
-    if (MU == 0) {
-      h0[c] = h2_axpy_r(m_r, v.z, v.x);
-      h1[c] = h2_axpy_r(m_r, v.w, v.y);
-    } else if (MU == 1) {
-      h0[c] = h2_axpy_i(m_i, v.w, v.x);
-      h1[c] = h2_axpy_i(m_i, v.z, v.y);
-    } else if (MU == 2) {
-      h0[c] = h2_axpy_r(m_r, v.w, v.x);
-      h1[c] = h2_axpy_r(p_r, v.z, v.y);
-    } else {
-      h0[c] = h2_axpy_i(m_i, v.z, v.x);
-      h1[c] = h2_axpy_i(p_i, v.w, v.y);
-    }
-    g0[c] = h2u(__hmul2(rot, __lowhigh2highlow(u2h(h0[c]))));
-    g1[c] = h2u(__hmul2(rot, __lowhigh2highlow(u2h(h1[c]))));
+    project_h2<MU>(sig, __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j), h0[c], h1[c]);
+    g0[c] = rot_h2<ADJ>(h0[c]);
+    g1[c] = rot_h2<ADJ>(h1[c]);
   }
   const unsigned *lu = reinterpret_cast<const unsigned *>(lk);
 #pragma unroll
@@ -193,26 +203,10 @@ template <int D, int MU, bool ADJ>
 __device__ __forceinline__ void hop_dir_f16_real(cx<float> acc[D][4], const void *in, int64_t Vh, int64_t j,
                                                  const void *lk, int64_t li, float sig, float scl) {
   constexpr int NC = (D * D + 1) / 2;
-  const __half2 m_r = __float2half2_rn(-sig), p_r = __float2half2_rn(sig);
-  const __half2 m_i = __floats2half2_rn(sig, -sig), p_i = __floats2half2_rn(-sig, sig);
   unsigned h0[D], h1[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j);
-    if (MU == 0) {
-      h0[c] = h2_axpy_r(m_r, v.z, v.x);
-      h1[c] = h2_axpy_r(m_r, v.w, v.y);
-    } else if (MU == 1) {
-      h0[c] = h2_axpy_i(m_i, v.w, v.x);
-      h1[c] = h2_axpy_i(m_i, v.z, v.y);
-    } else if (MU == 2) {
-      h0[c] = h2_axpy_r(m_r, v.w, v.x);
-      h1[c] = h2_axpy_r(p_r, v.z, v.y);
-    } else {
-      h0[c] = h2_axpy_i(m_i, v.z, v.x);
-      h1[c] = h2_axpy_i(p_i, v.w, v.y);
-    }
-  }
+  for (int c = 0; c < D; ++c)
+    project_h2<MU>(sig, __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j), h0[c], h1[c]);
   const unsigned *lu = reinterpret_cast<const unsigned *>(lk);
   unsigned u[NC];
 #pragma unroll

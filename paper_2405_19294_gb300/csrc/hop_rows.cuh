@@ -13,7 +13,9 @@
 //   1. warp w loads colours c = w R ... of psi(j) for its 32 sites, projects
 //      them (Sec. 2.2) and stores h0[c], h1[c] to shared memory laid out
 //      [colour][lane] (double-buffered per neighbour; colours up to a multiple
-//      of the column batch CB, the pad kept at zero);
+//      of the column batch CB, the pad kept at zero).  FP16 fields with real
+//      links stage h0, h1 as half2, and the products are f16 x f16 -> f32
+//      FMAs on the FP16 link entries;
 //   2. one block barrier; then each warp walks the colours in batches of CB:
 //      it first issues all R x CB link loads of the batch (independent, so
 //      they are in flight together), then multiplies them with the staged
@@ -113,6 +115,41 @@ __device__ __forceinline__ void rows_mul(const cx<typename PT<P>::A> *hs, int la
   }
 }
 
+// FP16 form of rows_mul for real links: the staged half-spinors are
+// [colour][lane] uint2 = (h0, h1) as half2; the link entries stay FP16, and
+// every product is an f16 x f16 -> f32 FMA
+template <int D, bool REAL, int R>
+__device__ __forceinline__ void rows_mul_f16(const uint2 *hs, int lane, const int ar[R], const void *lk, int64_t li,
+                                             int64_t Vh, cx<float> r0[R], cx<float> r1[R]) {
+  static_assert(REAL, "complex links take rows_mul");
+  typedef RowsGeom<D, REAL, R> G;
+  constexpr int CB = G::CB;
+  constexpr int ROWCH = G::DP / 2;
+  const unsigned *rp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) rp[r] = reinterpret_cast<const unsigned *>(lk) + (size_t)(ar[r] * ROWCH) * (size_t)Vh + li;
+#pragma unroll 1
+  for (int c0 = 0; c0 < G::DC; c0 += CB) {
+    unsigned u[R][CB / 2];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < CB / 2; ++q) u[r][q] = __ldg(rp[r] + (int64_t)((c0 >> 1) + q) * Vh);
+#pragma unroll
+    for (int cc = 0; cc < CB; ++cc) {
+      const uint2 h = hs[(c0 + cc) * 32 + lane];
+      const bool hi = (cc & 1) != 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        r0[r].x = fma_f16(u[r][cc >> 1], h.x, r0[r].x, hi, false);
+        r0[r].y = fma_f16(u[r][cc >> 1], h.x, r0[r].y, hi, true);
+        r1[r].x = fma_f16(u[r][cc >> 1], h.y, r1[r].x, hi, false);
+        r1[r].y = fma_f16(u[r][cc >> 1], h.y, r1[r].y, hi, true);
+      }
+    }
+  }
+}
+
 // Zero the pad colours D ... DC-1 of both half-spinor buffers; called once at
 // kernel start, before the first tile's first barrier.  No tile writes them.
 template <int D, bool REAL, int P, int R>
@@ -120,7 +157,16 @@ __device__ __forceinline__ void rows_zero_pads(unsigned char *smem) {
   typedef typename PT<P>::A A;
   typedef RowsGeom<D, REAL, R> G;
   constexpr int DC = G::DC;
-  if constexpr (DC > D) {
+  if constexpr (DC > D && P == 2 && REAL) {
+    // FP16 with real links stages [colour][lane] uint2 = (h0, h1): zero from
+    // colour D to the end of each buffer
+    uint2 *sh = reinterpret_cast<uint2 *>(smem);
+    constexpr int PER = 2 * DC * 32 - D * 32;  // uint2 entries per buffer from colour D on
+    for (int e = threadIdx.x; e < 2 * PER; e += G::NT) {
+      const int buf = e / PER, rem = e % PER;
+      sh[buf * (2 * DC * 32) + D * 32 + rem] = make_uint2(0u, 0u);
+    }
+  } else if constexpr (DC > D) {
     cx<A> *sh = reinterpret_cast<cx<A> *>(smem);
     for (int e = threadIdx.x; e < 2 * 2 * (DC - D) * 32; e += G::NT) {
       const int buf = e / (2 * (DC - D) * 32), rem = e % (2 * (DC - D) * 32);
@@ -138,6 +184,10 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
   constexpr int W = G::W;
   constexpr int DC = G::DC;
   cx<A> *sh = reinterpret_cast<cx<A> *>(smem);  // [2][2 DC][32]
+  // FP16 with real links: half2 staging and f16 x f16 -> f32 FMAs (the adjoint
+  // classes ran 7-76 % faster).  Complex links convert to FP32 on load: with
+  // four mixed FMAs per complex entry the large sym classes ran 9-27 % slower.
+  constexpr bool F16MIX = (P == 2) && REAL;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int a0 = w * R;
@@ -198,25 +248,45 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
     const A sig = bwd ? sg : -sg;
     const A scl = (P == 2) ? (A)isc[j] : A(1);
     cx<A> *hs = sh + (n & 1) * (2 * DC * 32);
-    // 1. project this warp's colours of psi(j)
+    // 1. project this warp's colours of psi(j) (FP16 with real links: in half2,
+    // unscaled; the neighbour's site scale joins the reconstruction)
+    if constexpr (F16MIX) {
+      uint2 *hu = reinterpret_cast<uint2 *>(hs);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int c = a0 + r;
-      if (c < D) {
-        cx<A> psi[4], h0, h1;
-        ld_colour<P>(in, Vh, j, c, psi);
-        switch (mu) {
-          case 0: project<0>(sig, psi, h0, h1); break;
-          case 1: project<1>(sig, psi, h0, h1); break;
-          case 2: project<2>(sig, psi, h0, h1); break;
-          default: project<3>(sig, psi, h0, h1); break;
+      for (int r = 0; r < R; ++r) {
+        const int c = a0 + r;
+        if (c < D) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + (int64_t)c * Vh + j);
+          uint2 h;
+          switch (mu) {
+            case 0: project_h2<0>(sig, v, h.x, h.y); break;
+            case 1: project_h2<1>(sig, v, h.x, h.y); break;
+            case 2: project_h2<2>(sig, v, h.x, h.y); break;
+            default: project_h2<3>(sig, v, h.x, h.y); break;
+          }
+          hu[c * 32 + lane] = h;
         }
-        if (P == 2) {
-          h0 = scale(scl, h0);
-          h1 = scale(scl, h1);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = a0 + r;
+        if (c < D) {
+          cx<A> psi[4], h0, h1;
+          ld_colour<P>(in, Vh, j, c, psi);
+          switch (mu) {
+            case 0: project<0>(sig, psi, h0, h1); break;
+            case 1: project<1>(sig, psi, h0, h1); break;
+            case 2: project<2>(sig, psi, h0, h1); break;
+            default: project<3>(sig, psi, h0, h1); break;
+          }
+          if (P == 2) {
+            h0 = scale(scl, h0);
+            h1 = scale(scl, h1);
+          }
+          hs[(2 * c) * 32 + lane] = h0;
+          hs[(2 * c + 1) * 32 + lane] = h1;
         }
-        hs[(2 * c) * 32 + lane] = h0;
-        hs[(2 * c + 1) * 32 + lane] = h1;
       }
     }
     __syncthreads();
@@ -226,15 +296,25 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
     cx<A> r0[R], r1[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) r0[r] = r1[r] = mk(A(0), A(0));
-    rows_mul<D, REAL, P, R>(hs, lane, ar, lk, ii, Vh, r0, r1);
+    if constexpr (F16MIX) rows_mul_f16<D, REAL, R>(reinterpret_cast<const uint2 *>(hs), lane, ar, lk, ii, Vh, r0, r1);
+    else rows_mul<D, REAL, P, R>(hs, lane, ar, lk, ii, Vh, r0, r1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (a0 + r < D) {
-        switch (mu) {
-          case 0: reconstruct<0>(sig, r0[r], r1[r], acc[r]); break;
-          case 1: reconstruct<1>(sig, r0[r], r1[r], acc[r]); break;
-          case 2: reconstruct<2>(sig, r0[r], r1[r], acc[r]); break;
-          default: reconstruct<3>(sig, r0[r], r1[r], acc[r]); break;
+        if constexpr (F16MIX) {
+          switch (mu) {
+            case 0: reconstruct_w<0>(sig, scl, r0[r], r1[r], acc[r]); break;
+            case 1: reconstruct_w<1>(sig, scl, r0[r], r1[r], acc[r]); break;
+            case 2: reconstruct_w<2>(sig, scl, r0[r], r1[r], acc[r]); break;
+            default: reconstruct_w<3>(sig, scl, r0[r], r1[r], acc[r]); break;
+          }
+        } else {
+          switch (mu) {
+            case 0: reconstruct<0>(sig, r0[r], r1[r], acc[r]); break;
+            case 1: reconstruct<1>(sig, r0[r], r1[r], acc[r]); break;
+            case 2: reconstruct<2>(sig, r0[r], r1[r], acc[r]); break;
+            default: reconstruct<3>(sig, r0[r], r1[r], acc[r]); break;
+          }
         }
       }
     }
