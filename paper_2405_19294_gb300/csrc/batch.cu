@@ -1,6 +1,6 @@
 // Many independent lattices (uneven volume, N and representation) solved
-// together: the batched operator and CG (SURVEY workload of 64 small
-// lattices; the paper notes that at small volumes kernel-call overhead
+// together: the batched operator and CG (for example 64 small lattices of
+// 8^4 to 16^3 x 32; the paper notes that at small volumes kernel-call overhead
 // dominates, Sec. 3.1.1 and Sec. 3.2).
 //
 // Lattices are grouped into classes of equal (d_R, real links); each class
