@@ -204,7 +204,9 @@ int hr_unpack_spinor(hr_lattice *lat, double *canonical, const void *internal, i
 /* out = Dhat_p in (parity EVEN/ODD) or D in (FULL), or the adjoint with
  * dagger = 1 (= g5 D g5), on `nrhs` internal fields of precision prec.
  * FP64 fields compute in FP64; FP32 and FP16 fields accumulate in FP32.
- * csw must equal the value given to hr_represent_links.  `in` and `out`
+ * With FP16 fields the projected half-spinor may be rounded to FP16 before
+ * the link product (FP16 x FP16 -> FP32 multiply-add); the relative error
+ * against FP64 stays about 3e-4 of the field norm.  csw must equal the value given to hr_represent_links.  `in` and `out`
  * must not overlap.  Two hopping launches, no host synchronisation. */
 int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,
             int prec, int nrhs, int dagger);
