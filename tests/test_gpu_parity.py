@@ -311,3 +311,23 @@ def test_torch_caching_allocator_backs_library_buffers(hr):
         hr.use_torch_allocator(False)
     lat2, _ = gpu_lattice(hr, 4, 4, 3, "fund", 1.0, 0.0)   # back on cudaMalloc
     lat2.close()
+
+
+@pytest.mark.parametrize("N,rep", [(3, "fund"), (2, "adj"), (3, "adj"), (3, "sym"), (5, "fund"), (4, "adj"),
+                                   (6, "adj")])
+def test_fp16_error_stays_near_storage_rounding(hr, N, rep):
+    """FP16 Dhat keeps the error of FP16 storage: the half2 projection and the
+    FP16 x FP16 -> FP32 products (site kernel; rows kernel for real links) add
+    one FP16 rounding of the half-spinor, measured at about 3e-4 relative.  A
+    bound of 1e-3, well inside the 5e-3 parity tolerance, catches an
+    accumulation that slipped to FP16."""
+    T, L, m0, eps = 4, 6, -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, 0.0)
+    op = oracle_operator(T, L, N, rep, eps, m0, 0.0)
+    psi = inputs.gaussian_spinor(3, T, L, lat.d)
+    mask = op.geom.parity == 0
+    ref = _oracle_apply(op, psi[0], 0, 0)
+    for sh in lat.shape_candidates(2):
+        lat.set_shape(2, sh)
+        got = _gpu_apply(lat, psi, 0, m0, 0.0, 2, 0)[0]
+        assert rel_err(got, ref, mask) < 1e-3, sh
