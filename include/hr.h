@@ -32,6 +32,11 @@
  *   default stream) and is asynchronous unless stated otherwise.  Kernel-side
  *   guards latch a device error word, reported (HR_ERR_DEVICE) by the next
  *   synchronising call.
+ * - A lattice (or batch) handle is driven by one host thread at a time;
+ *   different handles may be driven from different threads (the autotuner's
+ *   shared table is locked), except for the calls whose scratch is
+ *   process-wide and which say so: hr_bicgstab_solve and hr_norm2_static.
+ *   hr_set_allocator is process-wide.
  * - Canonical layouts (what the caller sees), all FP64, complex as (re, im):
  *     site index   ((t*L + z)*L + y)*L + x,  direction 0 = t, 1..3 = x, y, z
  *     links        U[V][4][N][N]       complex, row-major
@@ -368,7 +373,9 @@ int hr_domain_hop_end(hr_lattice *lat, void *out, int out_parity, double m0, int
 int hr_domains_dphi(int n, hr_lattice *const *lats, void *const *out, const void *const *in, int parity, double m0,
                     int prec, int nrhs, int dagger);
 
-/* Human-readable text of an hr_status. */
+/* Human-readable text of an hr_status.  For HR_ERR_CUDA it names the failing
+ * CUDA call last seen by the calling host thread; the text stays valid until
+ * that thread's next CUDA error. */
 const char *hr_status_string(int status);
 
 #ifdef __cplusplus

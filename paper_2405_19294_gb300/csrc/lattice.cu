@@ -12,7 +12,8 @@
 
 #include "hr_internal.h"
 
-static char g_last_error[512];
+// detail of the last CUDA error seen by the calling host thread (hr_status_string)
+static thread_local char g_last_error[512];
 
 void hr_note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
