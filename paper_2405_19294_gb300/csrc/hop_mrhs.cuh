@@ -153,7 +153,9 @@ __device__ __forceinline__ void ld_half_colour(const void *f, int64_t Vh, int64_
 }
 
 // FP32 / FP16 kernels of d_R = 6 are held to 128 registers (two 256-thread
-// blocks' worth per SM), which their clover epilogue otherwise exceeds
+// blocks' worth per SM), which their clover epilogue otherwise exceeds.  For
+// the other classes 0 leaves the minimum unspecified, which compiles as the
+// one-argument form; an explicit 1 had raised their register counts.
 template <int D, int P>
 constexpr int mrhs_min_blocks() { return (P != 0 && D == 6) ? 2 : 0; }
 
