@@ -128,7 +128,7 @@ def run_reference(args):
             "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "SU(3) fund 32^3x64 Dhat even (sampled: 16x8^3 per step)",
-                       "T": WORKLOAD["T"], "L": WORKLOAD["L"]},
+                       "T": WORKLOAD["T"], "L": WORKLOAD["L"], "seeds": {"links": 0, "source": 1}},
             "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)",
                              "cores": 1, "kind": "oracle",
                              "sample": f"Dhat even on {T}x{L}^3 per step ({sites} even sites)"},
@@ -776,7 +776,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "SU(3) fund 32^3x64 Dhat even (even-odd Schur), eps=1.0 reunitarised, "
                                    "m0=-0.4", "T": T, "L": L, "N": N, "rep": rep,
-                       "l2": "flushed between steps (512 MiB read)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (512 MiB read)", "parallelism": f"replicas x{world}",
+                       "seeds": {"links": 0, "source": 1}},
             "roofline": roof,
             "gpu_launches": 2 * args.steps,
             "e2e": {"value": round(world * b32 / (e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
