@@ -47,3 +47,14 @@ def test_create_rejects_bad_shapes_before_touching_the_device():
     h = ctypes.c_void_p()
     for args in [(3, 4, 3, 0), (4, 3, 3, 0), (4, 4, 1, 0), (4, 4, 13, 0), (4, 4, 7, 1), (4, 4, 2, 3), (4, 4, 3, 9)]:
         assert lib.hr_lattice_create(*args, ctypes.byref(h)) == -1
+
+
+def test_shape_code_round_trip():
+    """The binding's launch-shape code (rows, mrhs, regs, G, block packed in
+    decimal fields, as hr.h documents) decodes back to the same tuple."""
+    from paper_2405_19294_gb300 import hr
+    for shape in [(0, 32, 1, 0, 0), (0, 256, 0, 0, 0), (16, 128, 0, 0, 0), (0, 0, 0, 16, 0), (0, 0, 0, 8, 0),
+                  (0, 576, 0, 0, 2), (0, 64, 2, 0, 0), (4, 128, 0, 0, 0), (0, 96, 0, 0, 5)]:
+        code = hr._shape_code(shape)
+        assert hr.Lattice._decode(code) == shape
+    assert hr._shape_code((0, 32, 1)) == hr._shape_code((0, 32, 1, 0, 0)) == 100032
