@@ -331,3 +331,23 @@ def test_fp16_error_stays_near_storage_rounding(hr, N, rep):
         lat.set_shape(2, sh)
         got = _gpu_apply(lat, psi, 0, m0, 0.0, 2, 0)[0]
         assert rel_err(got, ref, mask) < 1e-3, sh
+
+
+@pytest.mark.parametrize("N,rep,T,csw", [(2, "fund", 2, 0.0), (3, "fund", 2, 1.0), (2, "adj", 2, 0.0),
+                                         (3, "sym", 4, 0.0)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_dphi_parity_smallest_lattice(hr, N, rep, T, csw, prec):
+    """L = 2 (and T = 2): the forward and backward neighbours coincide, so the
+    two hops of each direction land on the same site and must both be added;
+    V/2 = 4 T sites, one ragged tile."""
+    L, m0, eps = 2, -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, csw)
+    op = oracle_operator(T, L, N, rep, eps, m0, csw)
+    psi = inputs.gaussian_spinor(5, T, L, lat.d)
+    g = op.geom
+    for parity in (0, 1, 2):
+        for dagger in (0, 1):
+            got = _gpu_apply(lat, psi, parity, m0, csw, prec, dagger)[0]
+            ref = _oracle_apply(op, psi[0], parity, dagger)
+            mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+            assert rel_err(got, ref, mask) < TOL[prec], (parity, dagger)
