@@ -172,23 +172,29 @@ class Lattice:
         return n.value
 
     def new_field(self, parity: int, prec: int, nrhs: int = 1):
+        """A zeroed internal field (uint8 device tensor of field_bytes bytes)."""
         import torch
         return torch.zeros(self.field_bytes(parity, prec, nrhs), dtype=torch.uint8, device="cuda")
 
     def pack(self, internal, canonical, parity: int, prec: int, nrhs: int = 1):
+        """Canonical FP64 spinors psi[nrhs][V][4][d][2] (device or page-locked host tensor) ->
+        internal field of the given parity and precision (hr_pack_spinor)."""
         _check(_lib.hr_pack_spinor(self._h, _ptr(internal), _ptr_or_pinned(canonical), parity, prec, nrhs),
                "hr_pack_spinor")
 
     def unpack(self, canonical, internal, parity: int, prec: int, nrhs: int = 1):
+        """Internal field -> canonical FP64 spinors; other-parity sites untouched (hr_unpack_spinor)."""
         _check(_lib.hr_unpack_spinor(self._h, _ptr_or_pinned(canonical), _ptr(internal), parity, prec, nrhs),
                "hr_unpack_spinor")
 
     # -- gauge -----------------------------------------------------------
     def links_from_algebra(self, U, a, eps: float, reunitarise: bool = True):
+        """U[V][4][N][N][2] = exp(i eps sum_k a_k T_k) from a[V][4][N^2-1] (both FP64 device tensors)."""
         _check(_lib.hr_links_from_algebra(self._h, _ptr(U), _ptr(a), eps, int(reunitarise)),
                "hr_links_from_algebra")
 
     def represent_links(self, U, reunitarise: bool = True, csw: float = 0.0):
+        """Build U_R (with the antiperiodic time sign) in every precision, and the clover term if csw != 0."""
         _check(_lib.hr_represent_links(self._h, _ptr(U), int(reunitarise), csw), "hr_represent_links")
 
     def export_represented_links(self, out):
@@ -204,6 +210,8 @@ class Lattice:
     # -- operator and solver ---------------------------------------------
     def dphi(self, out, inp, parity: int, m0: float, csw: float, prec: int, nrhs: int = 1,
              dagger: bool = False):
+        """out = Dhat_parity inp (EVEN/ODD) or D inp (FULL), or the adjoint; internal fields of
+        precision prec, nrhs back to back; queued on the lattice's stream (hr_dphi)."""
         _check(_lib.hr_dphi(self._h, _ptr(out), _ptr(inp), parity, m0, csw, prec, nrhs, int(dagger)),
                "hr_dphi")
 
@@ -251,6 +259,7 @@ class Lattice:
                                       _ptr(recv_up), _ptr(recv_down)), "hr_domain_hop_end")
 
     def norm2(self, x, parity: int, prec: int, nrhs: int = 1):
+        """|x_r|^2 per right-hand side, accumulated in FP64 (synchronous)."""
         out = (C.c_double * nrhs)()
         _check(_lib.hr_norm2(self._h, _ptr(x), parity, prec, nrhs, out), "hr_norm2")
         return list(out)
@@ -258,6 +267,9 @@ class Lattice:
     def cg_solve(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
                  inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,
                  raise_on_error: bool = True):
+        """Solve Dhat^+ Dhat x = b (D^+ D for FULL) to a true FP64 relative residual tol: plain FP64
+        CG, or FP64 defect correction around an FP32 / FP16 inner CG (hr_cg_solve).  Returns the
+        status and statistics; raises HrError on failure unless raise_on_error is False."""
         prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every)
         st = hr_cg_stats()
         rc = _lib.hr_cg_solve(self._h, _ptr(x), _ptr(b), parity, m0, csw, C.byref(prm), C.byref(st))
