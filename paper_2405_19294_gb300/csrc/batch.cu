@@ -305,9 +305,10 @@ static int fill_desc(hr_batch *b, int slot0, int prec, void *const *out, const v
 // Pick each class's launch shape by timing its candidates on stage 0 of the
 // uploaded descriptors (persistent multi-lattice launches).
 static int tune_classes(hr_batch *b, int prec, int slot0, cudaStream_t s) {
-  cudaEvent_t e0, e1;
-  HR_CUDA(cudaEventCreate(&e0));
-  HR_CUDA(cudaEventCreate(&e1));
+  HrEvent e0_owner, e1_owner;
+  HR_CUDA(cudaEventCreate(&e0_owner.e));
+  HR_CUDA(cudaEventCreate(&e1_owner.e));
+  cudaEvent_t e0 = e0_owner.e, e1 = e1_owner.e;
   for (auto &c : b->cls) {
     if (c.tuned[prec]) continue;
     HopShape shapes[HR_MAX_SHAPES];
@@ -334,8 +335,6 @@ static int tune_classes(hr_batch *b, int prec, int slot0, cudaStream_t s) {
     c.tuned[prec] = 1;
     HR_TRY(build_items(c, b->lats, prec));
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return HR_OK;
 }
 
@@ -393,8 +392,9 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 1e-2);
   cudaStream_t s = b->s;
   // order after the caller's stream
-  cudaEvent_t ev;
-  HR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HrEvent ev_owner;
+  HR_CUDA(cudaEventCreateWithFlags(&ev_owner.e, cudaEventDisableTiming));
+  cudaEvent_t ev = ev_owner.e;
   HR_CUDA(cudaEventRecord(ev, b->stream));
   HR_CUDA(cudaStreamWaitEvent(s, ev, 0));
   // workspaces and per-lattice descriptors
@@ -629,7 +629,6 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   }
   cudaGraphExecDestroy(exec);
   HR_CUDA(cudaStreamSynchronize(s));
-  HR_CUDA(cudaEventDestroy(ev));
   if (stats) {
     std::vector<int> it(n);
     HR_CUDA(cudaMemcpy(it.data(), b->iters, sizeof(int) * n, cudaMemcpyDeviceToHost));

@@ -271,7 +271,7 @@ __global__ void bi_xr_kernel(char *x, char *r, const char *p, const char *s, con
 // What an instantiated chunk graph depends on (lattice geometry and buffers,
 // operator parameters, launch shape): replayed only while all of it matches.
 struct BiGraphKey {
-  const void *lat, *links, *tmp, *clover;
+  const void *lat, *links, *rlinks, *tmp, *clover, *clover_inv;
   int T, L, d, prec, nrhs, parity, check_every, shape;
   const void *f;
   size_t fb;
@@ -390,8 +390,10 @@ static int bi_loop(BiCtx &c, const double *stop, int check_every, int maxit, int
   memset(&key, 0, sizeof(key));
   key.lat = c.lat;
   key.links = c.lat->links[c.prec];
+  key.rlinks = c.lat->rlinks[c.prec];
   key.tmp = c.lat->tmp;
   key.clover = clover ? c.lat->clover_A[c.prec == HR_F64 ? 0 : 1] : nullptr;
+  key.clover_inv = clover ? c.lat->clover_Ainv[c.prec == HR_F64 ? 0 : 1] : nullptr;
   key.T = c.lat->T;
   key.L = c.lat->L;
   key.d = c.lat->d;
@@ -462,6 +464,19 @@ static int bi_loop(BiCtx &c, const double *stop, int check_every, int maxit, int
   return status;
 }
 
+// Drop the cached chunk graphs captured on `lat`: called when the lattice is
+// destroyed, so that a later lattice that happens to get the same host and
+// device addresses never replays kernels bound to the freed buffers.
+void hr_bicgstab_forget(const hr_lattice *lat) {
+  if (!g_bi) return;
+  for (int k = 0; k < 2; ++k)
+    if (g_bi->exec[k] && g_bi->key[k].lat == lat) {
+      cudaGraphExecDestroy(g_bi->exec[k]);
+      g_bi->exec[k] = nullptr;
+      memset(&g_bi->key[k], 0, sizeof(g_bi->key[k]));
+    }
+}
+
 extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
                                  const hr_cg_params *prm, hr_cg_stats *st) {
   if (!lat || !x || !b || !prm || parity < HR_EVEN || parity > HR_FULL) return HR_ERR_ARG;
@@ -480,8 +495,9 @@ extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int pa
   if (csw != 0.0) HR_TRY(hr_clover_prepare(lat, m0));
   if (parity != HR_FULL) HR_TRY(hr_ensure_tmp(lat, fb64 * nrhs));
   cudaStream_t s = g_bi->s;
-  cudaEvent_t ev;
-  HR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HrEvent ev_owner;
+  HR_CUDA(cudaEventCreateWithFlags(&ev_owner.e, cudaEventDisableTiming));
+  cudaEvent_t ev = ev_owner.e;
   HR_CUDA(cudaEventRecord(ev, lat->stream));
   HR_CUDA(cudaStreamWaitEvent(s, ev, 0));
   HR_CUDA(cudaMemsetAsync(g_bi->iters, 0, sizeof(int) * BI_MAXRHS, s));
@@ -578,7 +594,6 @@ extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int pa
     HR_TRY(norms(rn2));
   }
   HR_CUDA(cudaStreamSynchronize(s));
-  HR_CUDA(cudaEventDestroy(ev));
   if (st) {
     int it[BI_MAXRHS];
     HR_CUDA(cudaMemcpy(it, g_bi->iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));

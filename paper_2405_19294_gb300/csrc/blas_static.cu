@@ -1,12 +1,11 @@
 // hr_norm2_static: the field-norm reduction with its scratch memory in a
 // fixed, file-scope device array instead of memory the library allocates.
 //
-// Who needs it: callers that must not call cudaMalloc/cudaFree -- code that
-// runs while a stream is being captured into a CUDA graph (allocation calls
-// are illegal or serialising there), code whose device memory all comes from
-// a framework's pool allocator (a raw cudaMalloc would bypass the pool and
-// can fail or fragment memory the pool believes it owns), and code running
-// in host callbacks or under a fixed memory budget decided up front.
+// Who needs it: callers that must not call cudaMalloc/cudaFree -- code whose
+// device memory all comes from a framework's pool allocator (a raw cudaMalloc
+// would bypass the pool and can fail or fragment memory the pool believes it
+// owns), code running under a fixed memory budget decided up front, and
+// real-time or embedded callers that forbid allocation after start-up.
 //
 // The reduction kernel is the one hr_norm2 uses (blas.cu); only where its
 // per-block partial sums and arrival counters live differs.  That scratch is

@@ -33,6 +33,7 @@
 struct CgGraphKey {
   int pr, pp, check_every, nrhs, parity, shape;
   const void *x, *r, *p, *Ap, *t, *tmp;
+  const void *links, *rlinks, *clover, *clover_inv;  // operator buffers the captured hops read
   size_t fbr, fbp;
   int64_t Vh;
   int nsub;
@@ -174,6 +175,10 @@ static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap
   key.Ap = Ap;
   key.t = t;
   key.tmp = c.lat->tmp;
+  key.links = c.lat->links[pp];
+  key.rlinks = c.lat->rlinks[pp];
+  key.clover = clover ? c.lat->clover_A[pp == HR_F64 ? 0 : 1] : nullptr;
+  key.clover_inv = clover ? c.lat->clover_Ainv[pp == HR_F64 ? 0 : 1] : nullptr;
   key.fbr = fr.fb;
   key.fbp = fp.fb;
   key.Vh = fr.Vh;
@@ -320,8 +325,9 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
   c.red.stop = S(w, S_STOP);
   c.red.iters = w->iters;
   // order after the caller's stream
-  cudaEvent_t ev;
-  HR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HrEvent ev_owner;
+  HR_CUDA(cudaEventCreateWithFlags(&ev_owner.e, cudaEventDisableTiming));
+  cudaEvent_t ev = ev_owner.e;
   HR_CUDA(cudaEventRecord(ev, lat->stream));
   HR_CUDA(cudaStreamWaitEvent(c.s, ev, 0));
   HR_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * HR_MAX_RHS, c.s));
@@ -501,7 +507,6 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
     }
   }
   HR_CUDA(cudaStreamSynchronize(c.s));
-  HR_CUDA(cudaEventDestroy(ev));
   if (st) {
     int it[HR_MAX_RHS];
     HR_CUDA(cudaMemcpy(it, w->iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));

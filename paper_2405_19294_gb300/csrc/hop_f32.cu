@@ -8,6 +8,7 @@
 
 int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh) {
   const int d = lat->d;
+  if (sh.mrhs >= HR_TC_MRHS) return hr_launch_hop_tc_f32(lat, a, s);
   if (sh.mrhs > 0) return hop_mrhs_dispatch<1>(lat, a, s, sh.mrhs);
   if (sh.rows > 0) return rows_dispatch<1>(lat, a, s, sh.rows);
   if (sh.split_g == 0) return hop_dispatch<1>(lat, a, s, sh.bs, sh.regs);

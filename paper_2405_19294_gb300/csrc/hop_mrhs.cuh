@@ -152,6 +152,81 @@ __device__ __forceinline__ void ld_half_colour(const void *f, int64_t Vh, int64_
   }
 }
 
+// The epilogue of the multi-rhs kernels for output site i (tile slot s) of the
+// right-hand side at byte offset roff: acc = coef * H, then HOP_SCALED
+// (clover: A^{-1} acc) or HOP_SELF (acc + A self, or diag * self without
+// clover), and the store; clover blocks staged in shared memory as
+// [chunk][S] (as hop_site does from global memory).
+template <int D, int P, int S, bool CLOVER>
+__device__ __forceinline__ void mrhs_epilogue(const HopK &k, cx<typename PT<P>::A> (&acc)[D][4], const char *cbuf,
+                                              int s, int64_t i, size_t roff) {
+  typedef typename PT<P>::A A;
+  const int64_t Vh = k.Vh;
+  void *out = reinterpret_cast<char *>(k.out) + roff;
+  const A coef = (A)k.coef;
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[c][r] = scale(coef, acc[c][r]);
+  if (k.mode == HOP_SCALED) {
+    if (CLOVER) clover_apply_staged<D, P, S>(cbuf, s, acc);
+  } else {
+    const void *self = reinterpret_cast<const char *>(k.self) + roff;
+    const A ssc = (P == 2) ? (A)f16_scales(self, Vh, D)[i] : A(1);
+    if (CLOVER) {
+      // acc += A self, chiral block by block (the self field is read in halves so
+      // that only one block's input and output are live next to acc)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        cx<A> v[2 * D], w[2 * D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          cx<A> h[2];
+          ld_half_colour<P>(self, Vh, i, c, b, h);
+          v[c] = (P == 2) ? scale(ssc, h[0]) : h[0];
+          v[D + c] = (P == 2) ? scale(ssc, h[1]) : h[1];
+        }
+        clover_block_staged<D, P, S>(cbuf, s, b, v, w);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[c][2 * b + sp] = acc[c][2 * b + sp] + w[sp * D + c];
+      }
+    } else {
+      const A dg = (A)k.diag;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        cx<A> sv[4];
+        ld_colour<P>(self, Vh, i, c, sv);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[c][r] = axpy_r(dg, (P == 2) ? scale(ssc, sv[r]) : sv[r], acc[c][r]);
+      }
+    }
+  }
+  if (P == 0) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[c]));
+  } else if (P == 1) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) st_colour32(out, Vh, i, c, reinterpret_cast<const cx<float> *>(acc[c]));
+  } else {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) m = fmaxf(m, fmaxf(fabsf((float)acc[c][r].x), fabsf((float)acc[c][r].y)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      cx<float> v[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[r] = mk((float)acc[c][r].x * inv, (float)acc[c][r].y * inv);
+      st_colour16(out, Vh, i, c, v);
+    }
+    f16_scales_w(out, Vh, D)[i] = m;
+  }
+}
+
 // FP32 / FP16 kernels of d_R = 6 are held to 128 registers (two 256-thread
 // blocks' worth per SM), which their clover epilogue otherwise exceeds.  For
 // the other classes 0 leaves the minimum unspecified, which compiles as the
@@ -226,7 +301,6 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
   };
   const size_t roff = (size_t)(rhs < k.nrhs ? rhs : 0) * k.stride;
   const void *in = reinterpret_cast<const char *>(k.in) + roff;
-  void *out = reinterpret_cast<char *>(k.out) + roff;
   const A sg = (A)k.sgn;
   const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
   cx<A> acc[D][4];
@@ -271,69 +345,7 @@ __global__ void __launch_bounds__(256, mrhs_min_blocks<D, P>()) hop_mrhs_kernel(
   cp_async_wait<0>();
   __syncthreads();
   if (!active) return;
-  // ---- epilogue (as hop_site, clover from shared memory) ----
-  const A coef = (A)k.coef;
-#pragma unroll
-  for (int c = 0; c < D; ++c)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) acc[c][r] = scale(coef, acc[c][r]);
-  if (k.mode == HOP_SCALED) {
-    if (CLOVER) clover_apply_staged<D, P, S>(cbuf, s, acc);
-  } else {
-    const void *self = reinterpret_cast<const char *>(k.self) + roff;
-    const A ssc = (P == 2) ? (A)f16_scales(self, Vh, D)[i] : A(1);
-    if (CLOVER) {
-      // acc += A self, chiral block by block (the self field is read in halves so
-      // that only one block's input and output are live next to acc)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        cx<A> v[2 * D], w[2 * D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          cx<A> h[2];
-          ld_half_colour<P>(self, Vh, i, c, b, h);
-          v[c] = (P == 2) ? scale(ssc, h[0]) : h[0];
-          v[D + c] = (P == 2) ? scale(ssc, h[1]) : h[1];
-        }
-        clover_block_staged<D, P, S>(cbuf, s, b, v, w);
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-          for (int c = 0; c < D; ++c) acc[c][2 * b + sp] = acc[c][2 * b + sp] + w[sp * D + c];
-      }
-    } else {
-      const A dg = (A)k.diag;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        cx<A> sv[4];
-        ld_colour<P>(self, Vh, i, c, sv);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[c][r] = axpy_r(dg, (P == 2) ? scale(ssc, sv[r]) : sv[r], acc[c][r]);
-      }
-    }
-  }
-  if (P == 0) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[c]));
-  } else if (P == 1) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) st_colour32(out, Vh, i, c, reinterpret_cast<const cx<float> *>(acc[c]));
-  } else {
-    float m = 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) m = fmaxf(m, fmaxf(fabsf((float)acc[c][r].x), fabsf((float)acc[c][r].y)));
-    const float inv = m > 0.f ? 1.0f / m : 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      cx<float> v[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) v[r] = mk((float)acc[c][r].x * inv, (float)acc[c][r].y * inv);
-      st_colour16(out, Vh, i, c, v);
-    }
-    f16_scales_w(out, Vh, D)[i] = m;
-  }
+  mrhs_epilogue<D, P, S, CLOVER>(k, acc, cbuf, s, i, roff);
 }
 
 template <int D, bool REAL, int P, int S>

@@ -82,6 +82,18 @@ struct hr_lattice {
   } while (0)
 
 void hr_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// A CUDA event owned by the enclosing scope: every return path (including the
+// early returns of HR_TRY / HR_CUDA) releases it.
+struct HrEvent {
+  cudaEvent_t e = nullptr;
+  HrEvent() = default;
+  HrEvent(const HrEvent &) = delete;
+  HrEvent &operator=(const HrEvent &) = delete;
+  ~HrEvent() {
+    if (e) cudaEventDestroy(e);
+  }
+};
 // library-owned large buffers: through the allocator of hr_set_allocator, else cudaMalloc
 int hr_dev_alloc(void **p, size_t bytes);
 void hr_dev_free(void *p);
@@ -146,7 +158,10 @@ struct HopArgs {
 // 2: at most ~85 registers); split_g = G > 0 is the colour-split kernel with
 // G threads per site (128 threads per block).
 // mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
-// links staged once per site for all right-hand sides of the block).
+// links staged once per site for all right-hand sides of the block);
+// mrhs = HR_TC_MRHS + 16 the tensor-core multi-right-hand-side kernel
+// (hop_tc.cuh: 16 sites per block, the link products of up to 16 rhs as MMA
+// tiles; FP32 and FP16, complex d_R = 3 ... 6).
 // rows = R > 0 selects the rows kernel: R output colour rows per warp,
 // ceil(d/R) warps per block, 32 sites per block on the lanes.
 struct HopShape {
@@ -166,6 +181,7 @@ static inline int hr_shape_tile(const HopShape &s) {
   return s.rows ? 32 : (s.split_g ? 128 / s.split_g : s.bs);
 }
 #define HR_MAX_SHAPES 24
+#define HR_TC_MRHS 50
 
 // largest N of SU(N) (fundamental representation; the 2-index ones stop at 6)
 #define HR_MAX_NC 12
@@ -213,6 +229,12 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+// tensor-core multi-rhs kernel (complex d_R = 3 ... 6), FP32 (3xTF32) / FP16
+int hr_launch_hop_tc_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+int hr_launch_hop_tc_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
+static inline bool hr_has_tc_mrhs(int d, int is_real, int prec) {
+  return !is_real && d >= 3 && d <= 6 && prec != HR_F64;
+}
 
 // multi-lattice persistent hop (descs: one HopK per lattice; items: (lattice, tile))
 struct HopK;

@@ -178,10 +178,12 @@ extern "C" int hr_lattice_create_domain(int T_loc, int L, int N, int rep, int t0
 }
 
 void hr_cg_free(hr_lattice *lat);
+void hr_bicgstab_forget(const hr_lattice *lat);
 
 extern "C" int hr_lattice_destroy(hr_lattice *lat) {
   if (!lat) return HR_ERR_ARG;
   cudaDeviceSynchronize();  // the solver streams too: nothing may still use what is freed below
+  hr_bicgstab_forget(lat);
   for (int p = 0; p < 3; ++p) {
     hr_dev_free(lat->links[p]);
     hr_dev_free(lat->rlinks[p]);

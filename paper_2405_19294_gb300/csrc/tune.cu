@@ -22,6 +22,8 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
   int n = 0;
   const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 8);
   const bool site_mrhs = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
+  if (multi_rhs && hr_has_tc_mrhs(d, is_real, prec))
+    out[n++] = HopShape{0, 0, 0, HR_TC_MRHS + 16};  // link products of all rhs as MMA tiles
   if (site_mrhs && multi_rhs) {
     // links staged once per site for all right-hand sides of a block
     out[n++] = HopShape{0, 0, 0, 16};
@@ -106,9 +108,10 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone || n == 1 ||
       !tuning_enabled())
     return launch_shape(lat, prec, a, s, shapes[0]);
-  cudaEvent_t e0, e1;
-  HR_CUDA(cudaEventCreate(&e0));
-  HR_CUDA(cudaEventCreate(&e1));
+  HrEvent e0_owner, e1_owner;
+  HR_CUDA(cudaEventCreate(&e0_owner.e));
+  HR_CUDA(cudaEventCreate(&e1_owner.e));
+  cudaEvent_t e0 = e0_owner.e, e1 = e1_owner.e;
   // two sweeps over the candidates (the second in reverse order, so that no
   // shape always runs right after the same neighbour); each candidate keeps
   // the faster of its two timings of 4 launches
@@ -133,8 +136,6 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
       best_ms = t[c];
       best = shapes[c];
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_best[key] = best;

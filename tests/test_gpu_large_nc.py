@@ -80,7 +80,10 @@ def test_cg_large_nc(hr):
     lat.synchronize()
     x = to_complex(out)[0]
     r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
-    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10, st
+    # the library stops on its own FP64 true residual <= 1e-10; the oracle's independent
+    # evaluation of b - M x differs from it by rounding only, hence the 5 % margin
+    assert st["true_residual"] <= 1e-10, st
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10, st
 
 
 def test_lattice_rejects_large_nc_two_index(hr):

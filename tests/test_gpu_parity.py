@@ -167,13 +167,19 @@ def test_norm2(hr, prec, parity):
 
 
 def test_multi_rhs_dphi_matches_single(hr):
+    """Every multi-rhs launch shape gives each rhs the single-rhs result to the FP32
+    rounding level (the kernels differ in summation order, register budget and, for
+    the tensor-core kernel, the TF32 splitting)."""
     T, L, N, rep, m0 = 4, 4, 3, "fund", -0.4
     lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
     psi = inputs.gaussian_spinor(5, T, L, lat.d, nrhs=3)
-    many = _gpu_apply(lat, psi, 0, m0, 0.0, 1, 0, nrhs=3)
-    for r in range(3):
-        one = _gpu_apply(lat, psi[r:r + 1], 0, m0, 0.0, 1, 0, nrhs=1)[0]
-        assert np.array_equal(many[r], one)
+    ones = [_gpu_apply(lat, psi[r:r + 1], 0, m0, 0.0, 1, 0, nrhs=1)[0] for r in range(3)]
+    mask = Geometry(T, L).parity == 0
+    for sh in lat.shape_candidates(1, nrhs=3):
+        lat.set_shape(1, sh, nrhs=3)
+        many = _gpu_apply(lat, psi, 0, m0, 0.0, 1, 0, nrhs=3)
+        for r in range(3):
+            assert rel_err(many[r], ones[r], mask) < 1e-6, sh
 
 
 def test_errors_are_reported(hr):
@@ -351,3 +357,30 @@ def test_dphi_parity_smallest_lattice(hr, N, rep, T, csw, prec):
             ref = _oracle_apply(op, psi[0], parity, dagger)
             mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
             assert rel_err(got, ref, mask) < TOL[prec], (parity, dagger)
+
+
+TC_SHAPE = (0, 0, 0, 66, 0)    # tensor-core multi-rhs kernel (16 sites per block)
+
+
+@pytest.mark.parametrize("N,rep,csw", [(3, "sym", 1.0), (4, "asym", 0.0), (4, "fund", 1.0), (3, "fund", 0.0),
+                                       (5, "fund", 0.0)])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_core_multi_rhs(hr, N, rep, csw, prec):
+    """The tensor-core multi-rhs kernel against the oracle: 12 rhs (three 4-rhs MMA
+    tiles) and 17 rhs (a full 16-rhs block plus a block of one), Schur and full
+    operator, both signs, on 6^4 (V/2 = 648 = 40.5 tiles of 16: a ragged last tile)."""
+    T, L, m0, eps = 6, 6, -0.35, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, csw)
+    op = oracle_operator(T, L, N, rep, eps, m0, csw)
+    g = op.geom
+    assert TC_SHAPE in [tuple(s) for s in lat.shape_candidates(prec, nrhs=12, clover=csw != 0.0)]
+    for nrhs, cases in ((12, ((0, 0), (0, 1), (2, 0))), (17, ((1, 1),))):
+        psi = inputs.gaussian_spinor(13, T, L, lat.d, nrhs)
+        lat.set_shape(prec, TC_SHAPE, nrhs=nrhs, clover=csw != 0.0)
+        for parity, dagger in cases:
+            got = _gpu_apply(lat, psi, parity, m0, csw, prec, dagger, nrhs=nrhs)
+            mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+            for r in range(nrhs):
+                ref = _oracle_apply(op, psi[r], parity, dagger)
+                err = rel_err(got[r], ref, mask)
+                assert err < (1e-6 if prec == 1 else 1e-3), (nrhs, parity, dagger, r, err)

@@ -1,12 +1,13 @@
 """hr_norm2_static: the norm reduction for callers that cannot allocate.
 
-Some callers cannot call cudaMalloc/cudaFree: code that runs while a stream
-is captured into a CUDA graph, code whose device memory all comes from a
-framework's pool allocator, code in host callbacks or under a fixed memory
-budget.  hr_norm2_static keeps its reduction scratch in a fixed device array
-inside the library instead of allocating it.  This test calls it through the
-C ABI twice in a row and checks both results against hr_norm2 (the entry
-point that allocates its scratch), within the FP64 parity tolerance.
+Some callers cannot call cudaMalloc/cudaFree: code whose device memory all
+comes from a framework's pool allocator, code under a fixed memory budget,
+real-time callers that forbid allocation after start-up.  hr_norm2_static
+keeps its reduction scratch in a fixed device array inside the library
+instead of allocating it.  This test calls it through the C ABI twice in a
+row and checks both results against hr_norm2 (the entry point that allocates
+its scratch) and against a NumPy sum over the unpacked field, which shares no
+code with either reduction, within the FP64 parity tolerance.
 
 The file name makes pytest collect it last, so a run that stops at the first
 failure has already run every other test.
@@ -16,7 +17,8 @@ import ctypes
 import numpy as np
 import pytest
 
-from gpu_helpers import from_complex, gpu_lattice
+from gpu_helpers import from_complex, gpu_lattice, to_complex
+from oracle.dirac import Geometry
 from paper_2405_19294_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -31,6 +33,13 @@ def test_norm2_static_matches_allocating_entry_point(hr, parity, prec, nrhs):
     f = lat.new_field(parity, prec, nrhs)
     lat.pack(f, from_complex(psi), parity, prec, nrhs)
     ref = np.array(lat.norm2(f, parity, prec, nrhs))
+    # the stored field read back to FP64 on the host, summed by NumPy
+    back = torch.zeros((nrhs, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(back, f, parity, prec, nrhs)
+    lat.synchronize()
+    g = Geometry(T, L)
+    mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+    host = np.array([np.sum(np.abs(to_complex(back)[r, mask]) ** 2) for r in range(nrhs)])
     lib = hr.lib_handle()
     stream = torch.cuda.current_stream()
     for _ in range(2):
@@ -41,6 +50,7 @@ def test_norm2_static_matches_allocating_entry_point(hr, parity, prec, nrhs):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.all(np.abs(got - ref) <= 1e-13 * ref), (got, ref)
+        assert np.all(np.abs(got - host) <= 1e-13 * host), (got, host)
 
 
 def test_norm2_static_rejects_too_many_rhs(hr):
