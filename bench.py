@@ -12,8 +12,9 @@ the FP64 Dhat, the end-to-end number through the C ABI with host buffers, and
 CG on Dhat^+ Dhat to a true FP64 relative residual of 1e-10 (plain FP64,
 FP32-inner and FP16-inner mixed precision).
 
---impl reference times the FP64 CPU oracle on the host instead (bounded
-sample: the same operator on a 16 x 8^3 lattice per step) in the same unit.
+--impl reference times the FP64 CPU oracle on all host cores instead (bounded
+sample: the same operator on a 32 x 16^3 lattice per step, its even sites
+split over one process per core) in the same unit.
 """
 from __future__ import annotations
 
@@ -32,7 +33,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "Dphi GB/s (% of HBM peak) + CG time-to-1e-10, mixed/multi-RHS vs FP64"
 WORKLOAD = dict(T=64, L=32, N=3, rep="fund", eps=1.0, m0=-0.4, csw=0.0)
-SAMPLE = dict(T=16, L=8)   # bounded CPU sample for the oracle legs
+SAMPLE = dict(T=32, L=16)  # bounded CPU sample for the oracle legs
 
 
 def bytes_per_even_site(N, rep, w):
@@ -98,67 +99,123 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- reference arm --
-def run_reference(args):
-    """The FP64 oracle on the host: Dhat on the bounded sample lattice per step."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
+# The FP64 oracle on the host cores: the even Schur operator on a bounded
+# sample lattice, its even sites split into one contiguous block per worker
+# process (spawned, so that no worker inherits a CUDA context).  Every worker
+# builds the same seeded operator once; a step hands each worker its block.
+_ORACLE = {}
+
+
+def _oracle_init(T, L):
     from oracle import sun
     from oracle.dirac import Geometry, WilsonOperator
     from paper_2405_19294_gb300 import inputs
     wl = WORKLOAD
-    T, L = SAMPLE["T"], SAMPLE["L"]
     g = Geometry(T, L)
     a = inputs.algebra_coefficients(0, T, L, wl["N"])
     U = sun.reunitarise(sun.links_from_algebra(a, wl["eps"], wl["N"]))
     op = WilsonOperator(U, wl["N"], wl["rep"], g, wl["m0"], wl["csw"])
-    psi = inputs.gaussian_spinor(1, T, L, op.d)[0]
-    for _ in range(args.warmup):
-        op.apply_schur(psi, 0)
-    t = []
-    for _ in range(args.steps):
+    _ORACLE["op"] = op
+    _ORACLE["psi"] = inputs.gaussian_spinor(1, T, L, op.d)[0]
+
+
+def _oracle_block(sites):
+    op, psi = _ORACLE["op"], _ORACLE["psi"]
+    return op.apply_schur(psi, 0, sites=sites)[sites]
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OraclePool:
+    """One spawned worker per host core, each holding the sample operator."""
+
+    def __init__(self, T, L, cores=None):
+        import multiprocessing as mp
+        from oracle.dirac import Geometry
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"     # one thread per worker process
+        self.cores = cores or os.cpu_count() or 1
+        self.T, self.L = T, L
+        ev = Geometry(T, L).sites_of_parity(0)
+        self.sites = len(ev)
+        self.blocks = [b for b in np.array_split(ev, self.cores) if len(b)]
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init, initargs=(T, L))
+        self.pool.map(_oracle_block, self.blocks)    # every worker has built its operator
+
+    def dhat(self):
+        """One even Schur operator application over all blocks; wall seconds."""
         t0 = time.perf_counter()
-        op.apply_schur(psi, 0)
-        t.append(time.perf_counter() - t0)
+        self.pool.map(_oracle_block, self.blocks, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def describe(self, reps, sec):
+        return (f"Dhat even on {self.T}x{self.L}^3 ({self.sites} even sites) per step, split over "
+                f"{self.cores} worker processes (one per host core, {cpu_model()}); {reps} reps, "
+                f"{sec * 1e3:.1f} ms each")
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores: Dhat on the bounded sample lattice per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    T, L = SAMPLE["T"], SAMPLE["L"]
+    pool = OraclePool(T, L)
+    for _ in range(args.warmup):
+        pool.dhat()
+    t = [pool.dhat() for _ in range(args.steps)]
+    pool.close()
     ms = 1e3 * float(np.mean(t))
-    sites = g.V // 2
-    gbs = bytes_per_even_site(wl["N"], wl["rep"], 4) * sites / (ms * 1e-3) / 1e9
+    gbs = bytes_per_even_site(WORKLOAD["N"], WORKLOAD["rep"], 4) * pool.sites / (ms * 1e-3) / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "SU(3) fund 32^3x64 Dhat even (sampled: 16x8^3 per step)",
+            "config": {"workload": f"SU(3) fund 32^3x64 Dhat even (sampled: {T}x{L}^3 per step)",
                        "T": WORKLOAD["T"], "L": WORKLOAD["L"], "seeds": {"links": 0, "source": 1}},
             "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)",
-                             "cores": 1, "kind": "oracle",
-                             "sample": f"Dhat even on {T}x{L}^3 per step ({sites} even sites)"},
+                             "cores": pool.cores, "cpu": cpu_model(), "kind": "oracle",
+                             "sample": pool.describe(args.steps, ms * 1e-3)},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def cpu_baseline_leg():
-    """Time the oracle's Dhat on the bounded sample (about 10 s of CPU work)."""
-    from oracle import sun
-    from oracle.dirac import Geometry, WilsonOperator
-    from paper_2405_19294_gb300 import inputs
-    wl = WORKLOAD
+def cpu_baseline_leg(seconds=10.0):
+    """Time the oracle's Dhat on the bounded sample over all host cores (about 10 s)."""
     T, L = SAMPLE["T"], SAMPLE["L"]
-    g = Geometry(T, L)
-    a = inputs.algebra_coefficients(0, T, L, wl["N"])
-    U = sun.reunitarise(sun.links_from_algebra(a, wl["eps"], wl["N"]))
-    op = WilsonOperator(U, wl["N"], wl["rep"], g, wl["m0"], wl["csw"])
-    psi = inputs.gaussian_spinor(1, T, L, op.d)[0]
-    op.apply_schur(psi, 0)
+    pool = OraclePool(T, L)
+    pool.dhat()
     t0 = time.perf_counter()
     n = 0
-    while time.perf_counter() - t0 < 10.0:
-        op.apply_schur(psi, 0)
+    while time.perf_counter() - t0 < seconds:
+        pool.dhat()
         n += 1
     dt = (time.perf_counter() - t0) / n
-    gbs = bytes_per_even_site(wl["N"], wl["rep"], 4) * (g.V // 2) / dt / 1e9
-    return {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)", "cores": 1,
-            "kind": "oracle", "sample": f"Dhat even on {T}x{L}^3 ({g.V // 2} even sites), {n} reps, "
-                                        f"{dt * 1e3:.1f} ms each"}
+    pool.close()
+    gbs = bytes_per_even_site(WORKLOAD["N"], WORKLOAD["rep"], 4) * pool.sites / dt / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s (FP32-equivalent bytes of the same Dhat)",
+            "cores": pool.cores, "cpu": cpu_model(), "kind": "oracle", "sample": pool.describe(n, dt)}
 
 
 # ------------------------------------------------------- multi-process --
@@ -576,6 +633,182 @@ def _suite_c4(hr, inputs, torch):
     return line
 
 
+# ------------------------------------------------ the other workloads --
+# Measured inside the default bench run so that they carry its clock record;
+# every number is an operator or a whole solve on the GPU after a warm-up.
+def _ev_ms(torch, fn, reps, flush=None):
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.sum()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+
+def _cg_rec(res):
+    return {"seconds": round(res["wall_s"], 4), "iterations": res["iterations"], "outer_steps": res["outer_steps"],
+            "true_residual": res["true_residual"], "status": res["status"]}
+
+
+def _rel_diff(torch, lat, f_lo, prec, f64, nrhs=1):
+    """|D_prec psi - D_64 psi| / |D_64 psi| over the even sites (the FP64 operator is
+    the one held to 1e-13 of the oracle by the parity tests)."""
+    a = torch.zeros((nrhs, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    lat.unpack(a, f_lo, 0, prec, nrhs)
+    lat.unpack(b, f64, 0, 0, nrhs)
+    lat.synchronize()
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def config2(hr, inputs, torch, flush, peak):
+    """SU(2) adjoint and SU(4) antisymmetric, 24^3 x 48, m0 = -0.3: Dhat GB/s per
+    precision, and CG to 1e-10 (plain FP64, FP32 and FP16 inner solves)."""
+    T, L, m0 = 48, 24, -0.3
+    out = {}
+    for N, rep in ((2, "adj"), (4, "asym")):
+        lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, 0.0)
+        rec = {"lattice": "24^3x48", "d_R": lat.d, "m0": m0}
+        f64 = _pack_rhs(lat, inputs, torch, 1, T, L, 1, hr.F64)
+        o64 = lat.new_field(0, hr.F64)
+        lat.dphi(o64, f64, 0, m0, 0.0, hr.F64)
+        for prec, w in ((hr.F32, 4), (hr.F16, 2)):
+            fi = _pack_rhs(lat, inputs, torch, 1, T, L, 1, prec)
+            fo = lat.new_field(0, prec)
+            lat.dphi(fo, fi, 0, m0, 0.0, prec)
+            ms = _ev_ms(torch, lambda: lat.dphi(fo, fi, 0, m0, 0.0, prec), 20, flush)
+            gbs = bytes_per_even_site(N, rep, w) * lat.Vh / ms / 1e6
+            rec["dhat_" + ("fp32" if prec == hr.F32 else "fp16")] = {
+                "ms": round(ms, 4), "GBs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 3),
+                "shape": lat.tuned_shape(prec), "rel_err_vs_fp64": _rel_diff(torch, lat, fo, prec, o64)}
+        fx = lat.new_field(0, hr.F64)
+        cg = {}
+        for name, inner, itol in (("fp64", hr.F64, 0.0), ("mixed_fp32", hr.F32, 0.0),
+                                  ("mixed_fp16", hr.F16, 3e-3)):
+            cg[name] = _cg_rec(_timed_cg(lat, fx, f64, m0, 0.0, inner, inner_tol=itol))
+            if name != "fp64":
+                cg[name]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[name]["seconds"], 2)
+        cg["mixed_fp16"]["inner_tol"] = 3e-3
+        rec["cg"] = cg
+        out[f"SU({N}) {rep}"] = rec
+        lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def config3(hr, inputs, torch, flush, peak, nr=12):
+    """SU(3) sextet with clover (csw = 1), 32^3 x 64, m0 = -0.35, 12 right-hand
+    sides: the 12-rhs Dhat (one link and clover read per site for all rhs) in
+    FP32 and FP16, 12 single-rhs Dhat for comparison, and the 12-rhs CG per rhs
+    against a plain FP64 single-rhs solve."""
+    T, L, N, rep, m0, csw = 64, 32, 3, "sym", -0.35, 1.0
+    lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, csw)
+    d = lat.d
+    rec = {"lattice": "32^3x64", "d_R": d, "m0": m0, "csw": csw, "nrhs": nr}
+    fb = _pack_rhs(lat, inputs, torch, 1, T, L, nr, hr.F64)
+    o64 = lat.new_field(0, hr.F64, nr)
+    lat.dphi(o64, fb, 0, m0, csw, hr.F64, nr)
+    flops = nr * 2 * (128 * d * d + 56 * d + 64 * d * d - 8 * d) * lat.Vh
+    for prec, w in ((hr.F32, 4), (hr.F16, 2)):
+        fi = _pack_rhs(lat, inputs, torch, 1, T, L, nr, prec)
+        fo = lat.new_field(0, prec, nr)
+        lat.dphi(fo, fi, 0, m0, csw, prec, nr)
+        ms = _ev_ms(torch, lambda: lat.dphi(fo, fi, 0, m0, csw, prec, nr), 10, flush)
+        # links once per site for all rhs, A^{-1} and A once each, 5 spinor passes per rhs
+        scale_b = 5 * 4 * nr if w == 2 else 0
+        model = (16 * 2 * d * d * w + 2 * 8 * d * d * 4 + nr * 5 * 8 * d * w + scale_b) * lat.Vh
+        gbs = model / ms / 1e6
+        key = "fp32" if prec == hr.F32 else "fp16"
+        rec["dhat_12rhs_" + key] = {"ms": round(ms, 3), "model_bytes": int(model), "GBs": round(gbs, 1),
+                                    "frac_of_measured_hbm": round(gbs / peak, 3),
+                                    "TFLOPs": round(flops / ms / 1e9, 2),
+                                    "shape": lat.tuned_shape(prec, nrhs=nr, clover=True),
+                                    "rel_err_vs_fp64": _rel_diff(torch, lat, fo, prec, o64, nr)}
+        if prec == hr.F32:
+            fb1 = lat.field_bytes(0, prec, 1)
+            lat.dphi(fo[:fb1], fi[:fb1], 0, m0, csw, prec, 1)
+            ms1 = _ev_ms(torch, lambda: [lat.dphi(fo[r * fb1:(r + 1) * fb1], fi[r * fb1:(r + 1) * fb1], 0, m0, csw,
+                                                  prec, 1) for r in range(nr)], 5, flush)
+            rec["dhat_12x1rhs_fp32_ms"] = round(ms1, 3)
+        del fi, fo
+    del o64
+    for prec, k in ((hr.F32, nr), (hr.F16, nr), (hr.F64, 1)):
+        _warm(lat, prec, k, m0, csw)
+    fx = lat.new_field(0, hr.F64, nr)
+    cg = {}
+    r32 = _timed_cg(lat, fx, fb, m0, csw, hr.F32, nrhs=nr, reps=1)
+    cg["mixed_fp32_12rhs"] = dict(_cg_rec(r32), seconds_per_rhs=round(r32["wall_s"] / nr, 4))
+    r16 = _timed_cg(lat, fx, fb, m0, csw, hr.F16, nrhs=nr, inner_tol=3e-3, reps=1)
+    cg["mixed_fp16_12rhs"] = dict(_cg_rec(r16), seconds_per_rhs=round(r16["wall_s"] / nr, 4), inner_tol=3e-3)
+    fb1 = lat.new_field(0, hr.F64)
+    fx1 = lat.new_field(0, hr.F64)
+    fb1.copy_(fb[:lat.field_bytes(0, hr.F64, 1)])
+    r64 = _timed_cg(lat, fx1, fb1, m0, csw, hr.F64, reps=1)
+    cg["fp64_1rhs"] = _cg_rec(r64)
+    for k_ in ("mixed_fp32_12rhs", "mixed_fp16_12rhs"):
+        cg[k_]["per_rhs_speedup_vs_fp64"] = round(r64["wall_s"] / cg[k_]["seconds_per_rhs"], 2)
+    rec["cg"] = cg
+    lat.close()
+    del fb, fx, fb1, fx1
+    torch.cuda.empty_cache()
+    return rec
+
+
+def config4(hr, inputs, torch, nlat=64):
+    """64 lattices (8^4 ... 16^3 x 32, N = 2..6, mixed representations), m0 = -0.3:
+    one batched FP32 Dhat against 64 single-lattice launches (aggregate sites/s),
+    and the batched CG to 1e-8 against 64 single-lattice solves."""
+    shapes = inputs.batch_shapes(2, nlat)
+    lats, xs, bs, fi, fo = [], [], [], [], []
+    for k, (T, L, N, rep) in enumerate(shapes):
+        lt = _lattice(hr, inputs, torch, T, L, N, rep, 0.5, 0.0, seed=100 + k)
+        lats.append(lt)
+        bs.append(_pack_rhs(lt, inputs, torch, 200 + k, T, L, 1, hr.F64))
+        xs.append(lt.new_field(0, hr.F64))
+        fi.append(_pack_rhs(lt, inputs, torch, 200 + k, T, L, 1, hr.F32))
+        fo.append(lt.new_field(0, hr.F32))
+    batch = hr.Batch(lats)
+    m0s = [-0.3] * nlat
+    sites = sum(lt.Vh for lt in lats)
+    batch.dphi(fo, fi, 0, m0s, hr.F32)
+    for k, lt in enumerate(lats):
+        lt.dphi(fo[k], fi[k], 0, -0.3, 0.0, hr.F32)
+    tb = _ev_ms(torch, lambda: batch.dphi(fo, fi, 0, m0s, hr.F32), 10)
+    tp = _ev_ms(torch, lambda: [lt.dphi(fo[k], fi[k], 0, -0.3, 0.0, hr.F32) for k, lt in enumerate(lats)], 10)
+    rec = {"lattices": nlat, "even_sites": int(sites),
+           "dhat_fp32": {"batched_ms": round(tb, 4), "per_lattice_ms": round(tp, 4),
+                         "batched_sites_per_s": round(sites / tb * 1e3, 1),
+                         "per_lattice_sites_per_s": round(sites / tp * 1e3, 1),
+                         "speedup": round(tp / tb, 2)}}
+    batch.cg_solve(xs, bs, 0, m0s, 1e-8, inner_prec=hr.F32)     # warm-up: tuning, graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, st = batch.cg_solve(xs, bs, 0, m0s, 1e-8, inner_prec=hr.F32)
+    t_b = time.perf_counter() - t0
+    for k, lt in enumerate(lats):
+        lt.cg_solve(xs[k], bs[k], 0, -0.3, 0.0, 1e-8, inner_prec=hr.F32, raise_on_error=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per = [lt.cg_solve(xs[k], bs[k], 0, -0.3, 0.0, 1e-8, inner_prec=hr.F32, raise_on_error=False)
+           for k, lt in enumerate(lats)]
+    t_p = time.perf_counter() - t0
+    rec["cg_1e-8"] = {"status": rc, "batched_s": round(t_b, 4), "per_lattice_s": round(t_p, 4),
+                      "speedup": round(t_p / t_b, 2),
+                      "max_true_residual_batched": max(s_["true_residual"] for s_ in st),
+                      "max_true_residual_per_lattice": max(r["true_residual"] for r in per)}
+    batch.close()
+    for lt in lats:
+        lt.close()
+    torch.cuda.empty_cache()
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,6 +817,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the config 2/3/4 measurements")
     ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen,larged,blas: measure those workloads instead")
     ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
@@ -677,7 +911,17 @@ def main():
     for _ in range(3):
         lat.dphi(fout[hr.F64], fin[hr.F64], hr.EVEN, m0, csw, hr.F64)
     ms64 = float(np.mean(timed(hr.F64, max(3, args.steps // 4))))
-    clk = clocks.stop()
+    # FP16 Dhat (per-site scaled FP16 storage, FP32 arithmetic), unless it is the timed precision
+    peaks, kind = measured_peaks()
+    fp16 = None
+    if TP != hr.F16:
+        for _ in range(3):
+            lat.dphi(fout[hr.F16], fin[hr.F16], hr.EVEN, m0, csw, hr.F16)
+        ms16 = float(np.mean(timed(hr.F16, args.steps)))
+        g16 = bytes_per_even_site(N, rep, 2) * sites / (ms16 * 1e-3) / 1e9
+        fp16 = {"ms_per_step": round(ms16, 4), "GBs": round(g16, 2), "frac_of_measured_hbm": round(g16 / peaks["hbm_gbs"], 4),
+                "shape": lat.tuned_shape(hr.F16),
+                "rel_err_vs_fp64": _rel_diff(torch, lat, fout[hr.F16], hr.F16, fout[hr.F64])}
     b64 = bytes_per_even_site(N, rep, 8) * sites
     fl = flops_per_even_site(N, rep) * sites
 
@@ -764,7 +1008,13 @@ def main():
             for k in ("mixed_fp32", "mixed_fp16"):
                 cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[k]["seconds"], 2)
 
-    peaks, kind = measured_peaks()
+    # the other workloads (configs 2, 3, 4), inside the same clock record
+    configs = None
+    if not args.no_configs:
+        configs = {"c2": config2(hr, inputs, torch, flush, peaks["hbm_gbs"]),
+                   "c3": config3(hr, inputs, torch, flush, peaks["hbm_gbs"]),
+                   "c4": config4(hr, inputs, torch)}
+    clk = clocks.stop()
     traffic = ncu_traffic(f"dram_bytes_per_even_site_{args.prec}")
     roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(gbs / world / peaks["hbm_gbs"], 4), "peak_kind": kind,
@@ -786,7 +1036,7 @@ def main():
                             "overlap step k's kernels (copy streams, double-buffered staging)"},
             "fp64": {"ms_per_step": round(ms64, 4), "gbs": round(b64 / (ms64 * 1e-3) / 1e9, 2),
                      "tflops": round(fl / (ms64 * 1e-3) / 1e12, 3), "bound": "alu (FP64)"},
-            "cg": cg, "clocks": clk, "wall_timed_s": round(wall, 3)}
+            "fp16": fp16, "cg": cg, "configs": configs, "clocks": clk, "wall_timed_s": round(wall, 3)}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

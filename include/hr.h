@@ -125,21 +125,33 @@ int hr_set_allocator(hr_alloc_fn alloc, hr_free_fn release, void *ctx);
  * loaded.  Errors: HR_ERR_ARG.  (Sec. 3.1: any N_c and representation.) */
 int hr_lattice_create(int T, int L, int N, int rep, hr_lattice **out);
 
-/* Free the handle and everything the library allocated for it.  Synchronises. */
+/* Free the handle and everything the library allocated for it, and drop any
+ * cached solver graph captured on it.  Synchronises the device.  No
+ * counterpart in the paper (handle management).  Errors: HR_ERR_ARG (NULL). */
 int hr_lattice_destroy(hr_lattice *lat);
 
 /* Queue all further work of this lattice on `cuda_stream` (a cudaStream_t,
- * e.g. torch.cuda.current_stream().cuda_stream; NULL = legacy stream). */
+ * e.g. torch.cuda.current_stream().cuda_stream; NULL = legacy stream).  The
+ * caller owns the stream.  No counterpart in the paper (stream plumbing).
+ * Errors: HR_ERR_ARG (NULL lattice). */
 int hr_set_stream(hr_lattice *lat, void *cuda_stream);
 
-/* Sizes and the per-site work models. */
+/* Sizes and the per-site work models (written to *info, caller-owned host
+ * memory): d_R, real or complex links, V, V/2, flops of one hop per output
+ * site and ideal-reuse bytes of one hop per output site per precision.  The
+ * paper states that lattice codes are memory-bound and that the Dirac time
+ * tracks the bytes moved (Sec. 2.1, Sec. 3.1.1); these are the models the
+ * roofline uses.  Errors: HR_ERR_ARG. */
 int hr_lattice_info(const hr_lattice *lat, hr_info *info);
 
 /* Bytes of one internal spinor field: parity EVEN/ODD = one parity, FULL =
- * both; `nrhs` fields back to back. */
+ * both; `nrhs` fields back to back (written to *bytes, host).  No counterpart
+ * in the paper (layout query).  Errors: HR_ERR_ARG. */
 int hr_field_bytes(const hr_lattice *lat, int parity, int prec, int nrhs, size_t *bytes);
 
-/* Wait for the lattice's stream; report a latched device error (HR_ERR_DEVICE). */
+/* Wait for the lattice's stream; report a latched device error
+ * (HR_ERR_DEVICE) or a failed CUDA call (HR_ERR_CUDA).  No counterpart in the
+ * paper. */
 int hr_synchronize(hr_lattice *lat);
 
 /* ---- gauge field ------------------------------------------------------- */
@@ -189,7 +201,12 @@ int hr_set_clover_exponential(hr_lattice *lat, int on);
 /* ---- spinor fields ------------------------------------------------------ */
 
 /* Canonical FP64 spinors psi[nrhs][V][4][d] -> internal field of the given
- * parity and precision (device).  Only sites of that parity are read (both
+ * parity and precision (device, caller-owned, hr_field_bytes() bytes).  The
+ * internal layout is this library's own blocked structure of arrays; the
+ * paper's GPU fields are likewise strided, structure-of-arrays blocks
+ * (Sec. 2.1), in single or double precision (Sec. 3.2); FP16 with a per-site
+ * scale has no counterpart in the paper.  Errors: HR_ERR_ARG (NULL, bad enum,
+ * nrhs < 1, pageable host memory).  Only sites of that parity are read (both
  * for FULL).  `canonical` may be device memory or page-locked host memory
  * (cudaHostAlloc / cudaHostRegister / pinned torch tensors): the kernel then
  * reads the host buffer directly through its mapped address, so only that
@@ -199,15 +216,21 @@ int hr_pack_spinor(hr_lattice *lat, void *internal, const double *canonical, int
                    int prec, int nrhs);
 
 /* Internal field -> canonical FP64 spinors (device or page-locked host
- * memory, written directly as for hr_pack_spinor).  Sites of the other
- * parity are left untouched (set to zero first if that matters). */
+ * memory, written directly as for hr_pack_spinor; layouts of Sec. 2.1 as
+ * there).  Sites of the other parity are left untouched (set to zero first
+ * if that matters).  Errors: HR_ERR_ARG. */
 int hr_unpack_spinor(hr_lattice *lat, double *canonical, const void *internal, int parity,
                      int prec, int nrhs);
 
 /* ---- operator ------------------------------------------------------------ */
 
-/* out = Dhat_p in (parity EVEN/ODD) or D in (FULL), or the adjoint with
+/* The Wilson(-clover) Dirac operator of Sec. 3.1 (even-odd preconditioned,
+ * clover term as set at hr_represent_links), applied with the half-spinor
+ * projection of Sec. 2.2 (each neighbour is projected to two spin rows before
+ * the link product and rebuilt after it):
+ * out = Dhat_p in (parity EVEN/ODD) or D in (FULL), or the adjoint with
  * dagger = 1 (= g5 D g5), on `nrhs` internal fields of precision prec.
+ *   out, in : device internal fields (nrhs back to back; in read, out written)
  * FP64 fields compute in FP64; FP32 and FP16 fields accumulate in FP32.
  * With FP16 fields the projected half-spinor may be rounded to FP16 before
  * the link product (FP16 x FP16 -> FP32 multiply-add); the relative error
@@ -218,16 +241,33 @@ int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, d
 
 /* ---- linear algebra (Sec. 3.2) ------------------------------------------ */
 
-/* Global sums over internal fields, FP64 accumulation, deterministic order.
- * Result written to host memory; synchronises the stream. */
+/* Global sums |x_r|^2 over internal fields (the reductions of Sec. 3.2, which
+ * the paper runs as a site kernel plus a library reduction; here one kernel
+ * with a deterministic last-block sum), FP64 accumulation, fixed order.
+ *   x        : device internal field(s), nrhs back to back (read)
+ *   out_host : host double[nrhs] (written)
+ * Synchronises the stream.  Errors: HR_ERR_ARG, HR_ERR_CUDA. */
 int hr_norm2(hr_lattice *lat, const void *x, int parity, int prec, int nrhs,
              double *out_host);
 
+/* y_r = a_r x_r + b_r y_r for every rhs r (the site-wise linear algebra of
+ * Sec. 3.2, one fused launch), on internal fields of this lattice's geometry:
+ *   x, y : device internal fields of the same parity and precision, nrhs back
+ *          to back (x read, y read and written; x == y allowed)
+ *   a, b : host double[nrhs] (copied before the call returns)
+ * FP64 fields compute in FP64, FP32 / FP16 fields in FP32 (FP16 results
+ * re-encoded with their per-site scale).  Asynchronous on the lattice's stream.
+ * The building block of solvers driven from outside the library, such as the
+ * conjugate gradient over time slabs on several ranks.
+ * Errors: HR_ERR_ARG (NULL, bad enum, nrhs outside 1..64). */
+int hr_axpby(hr_lattice *lat, const void *x, void *y, const double *a, const double *b, int parity, int prec,
+             int nrhs);
+
 /* Variant of hr_norm2 that allocates nothing (the paper has no counterpart).
- * For callers that cannot call cudaMalloc/cudaFree: code running while a
- * stream is captured into a CUDA graph, code whose device memory all comes
- * from a framework's pool allocator, code in host callbacks or under a fixed
- * memory budget.  Its reduction scratch is a file-scope device array of about
+ * For callers that cannot call cudaMalloc/cudaFree: code whose device memory
+ * all comes from a framework's pool allocator, code under a fixed memory
+ * budget, real-time callers that forbid allocation after start-up.  Its
+ * reduction scratch is a file-scope device array of about
  * 312 KB (partial sums and arrival counters for up to 16 right-hand sides),
  * present on every GPU that loads the library until the process exits.
  *   x           : device, internal field(s) as for hr_norm2 (read)
@@ -266,8 +306,11 @@ typedef struct hr_batch hr_batch;
  * many lattices there are (kernel-call overhead at small volumes, Sec. 3.1.1).
  * Errors: HR_ERR_STATE (links missing), HR_ERR_UNSUPPORTED (clover). */
 int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out);
+/* Free the batch (not its lattices).  Synchronises.  No counterpart in the
+ * paper (handle management).  Errors: HR_ERR_ARG. */
 int hr_batch_destroy(hr_batch *batch);
-/* Stream the batch's work is ordered after (default: the first lattice's). */
+/* Stream the batch's work is ordered after (default: the first lattice's);
+ * a cudaStream_t owned by the caller.  No counterpart in the paper. */
 int hr_batch_set_stream(hr_batch *batch, void *cuda_stream);
 
 /* Pin the hopping launch shape of the class (d_R = d, real links is_real) at
@@ -276,14 +319,17 @@ int hr_batch_set_stream(hr_batch *batch, void *cuda_stream);
  * clover).  Errors: HR_ERR_ARG (no such class or shape). */
 int hr_batch_set_shape(hr_batch *batch, int d, int is_real, int prec, int shape);
 
-/* out[i] = Dhat_p in[i] (or its adjoint) on lattice i, parity EVEN or ODD,
+/* The even-odd Wilson operator of Sec. 3.1 on many small lattices at once
+ * (kernel-call overhead dominates small volumes, Sec. 3.1.1, Sec. 3.2):
+ * out[i] = Dhat_p in[i] (or its adjoint) on lattice i, parity EVEN or ODD,
  * bare mass m0[i] (host array); internal single-parity fields of precision
  * prec, one rhs each.  The first call per precision times each class's
  * launch shapes (outside stream capture). */
 int hr_batch_dphi(hr_batch *batch, void *const *out, const void *const *in, int parity, const double *m0,
                   int prec, int dagger);
 
-/* Solve (Dhat_p^+ Dhat_p) x[i] = b[i] on every lattice to a true FP64
+/* CG (Sec. 3.3) on many small lattices at once.
+ * Solve (Dhat_p^+ Dhat_p) x[i] = b[i] on every lattice to a true FP64
  * relative residual params->tol per lattice (x, b: FP64 internal fields;
  * x overwritten).  params->inner_prec HR_F32 or HR_F16: the inner CG of all
  * lattices runs in lock step as one CUDA graph per chunk of
@@ -294,11 +340,14 @@ int hr_batch_dphi(hr_batch *batch, void *const *out, const void *const *in, int 
 int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int parity, const double *m0,
                       const hr_cg_params *params, hr_cg_stats *stats);
 
-/* The hopping-kernel launch shape the autotuner chose for this lattice at
+/* Launch-shape autotuning (no counterpart in the paper, which fixes its kernel
+ * shapes at compile time, Sec. 2 and Sec. 3.1.2).
+ * The hopping-kernel launch shape the autotuner chose for this lattice at
  * (prec, nrhs, clover): rows * 100000000 + mrhs * 1000000 + regs * 100000 +
  * split_g * 1000 + threads per block.  mrhs = S > 0: the multi-right-hand-
  * side kernel with S sites per block (links staged once per site for all
- * right-hand sides); rows = R > 0: the rows kernel for large d_R (R output
+ * right-hand sides), mrhs = 66: the tensor-core multi-right-hand-side kernel
+ * (16 sites per block, link products as MMA tiles); rows = R > 0: the rows kernel for large d_R (R output
  * colour rows per warp, 32 sites per block on the lanes); otherwise
  * split_g = 0: one site per thread with register budget regs = 0 compiler's
  * choice, 1 up to ~170, 2 at most ~85 registers; split_g = G > 0: G threads
@@ -373,7 +422,8 @@ int hr_domain_hop_end(hr_lattice *lat, void *out, int out_parity, double m0, int
 int hr_domains_dphi(int n, hr_lattice *const *lats, void *const *out, const void *const *in, int parity, double m0,
                     int prec, int nrhs, int dagger);
 
-/* Human-readable text of an hr_status.  For HR_ERR_CUDA it names the failing
+/* Human-readable text of an hr_status (no counterpart in the paper; the
+ * returned string is library-owned, never NULL).  For HR_ERR_CUDA it names the failing
  * CUDA call last seen by the calling host thread; the text stays valid until
  * that thread's next CUDA error. */
 const char *hr_status_string(int status);

@@ -129,7 +129,8 @@ int hr_red_scratch(hr_lattice *lat, int nrhs) {
     HR_CUDA(cudaMalloc(&lat->red_partials, sizeof(double) * 2 * HR_RED_MAXBLK * HR_MAX_RHS));
     HR_CUDA(cudaMalloc(&lat->red_count, sizeof(unsigned) * HR_MAX_RHS));
     HR_CUDA(cudaMemset(lat->red_count, 0, sizeof(unsigned) * HR_MAX_RHS));
-    HR_CUDA(cudaMalloc(&lat->red_out, sizeof(double) * HR_MAX_RHS));
+    // red_out: [HR_MAX_RHS] results, then the a and b coefficients of hr_axpby
+    HR_CUDA(cudaMalloc(&lat->red_out, sizeof(double) * 3 * HR_MAX_RHS));
     HR_CUDA(cudaMallocHost(&lat->red_out_host, sizeof(double) * HR_MAX_RHS));
   }
   return HR_OK;
@@ -158,4 +159,29 @@ extern "C" int hr_norm2(hr_lattice *lat, const void *x, int parity, int prec, in
   HR_CUDA(cudaStreamSynchronize(lat->stream));
   for (int r = 0; r < nrhs; ++r) out_host[r] = lat->red_out_host[r];
   return HR_OK;
+}
+
+extern "C" int hr_axpby(hr_lattice *lat, const void *x, void *y, const double *a, const double *b, int parity,
+                        int prec, int nrhs) {
+  if (!lat || !x || !y || !a || !b || nrhs < 1 || nrhs > HR_MAX_RHS || prec < HR_F64 || prec > HR_F16 ||
+      parity < HR_EVEN || parity > HR_FULL)
+    return HR_ERR_ARG;
+  HR_TRY(hr_red_scratch(lat, nrhs));
+  // the coefficients go to the device through a pageable copy, which has
+  // taken them from the caller's arrays by the time it returns
+  double coef[2 * HR_MAX_RHS];
+  for (int r = 0; r < nrhs; ++r) {
+    coef[r] = a[r];
+    coef[HR_MAX_RHS + r] = b[r];
+  }
+  double *ad = lat->red_out + HR_MAX_RHS, *bd = lat->red_out + 2 * HR_MAX_RHS;
+  HR_CUDA(cudaMemcpyAsync(ad, coef, sizeof(double) * 2 * HR_MAX_RHS, cudaMemcpyHostToDevice, lat->stream));
+  FieldDesc f;
+  f.Vh = lat->Vh;
+  f.d = lat->d;
+  f.fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
+  f.nsub = parity == HR_FULL ? 2 : 1;
+  RedArgs red;
+  memset(&red, 0, sizeof(red));
+  return hr_blas_axpby(prec, prec, x, y, f, f, nrhs, ad, bd, red, 0, lat->stream);
 }

@@ -62,6 +62,7 @@ _SIGS = {
     "hr_norm2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "hr_cg_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(hr_cg_params),
                               C.POINTER(hr_cg_stats)]),
+    "hr_axpby": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int]),
     "hr_norm2_static": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "hr_tuned_shape": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "hr_hop_shape_candidates": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
@@ -263,6 +264,14 @@ class Lattice:
         out = (C.c_double * nrhs)()
         _check(_lib.hr_norm2(self._h, _ptr(x), parity, prec, nrhs, out), "hr_norm2")
         return list(out)
+
+    def axpby(self, x, y, a, b, parity: int, prec: int, nrhs: int = 1):
+        """y_r = a_r x_r + b_r y_r per rhs (a, b: scalars or sequences of nrhs floats)."""
+        av = a if hasattr(a, "__len__") else [a] * nrhs
+        bv = b if hasattr(b, "__len__") else [b] * nrhs
+        A = (C.c_double * nrhs)(*[float(v) for v in av])
+        B = (C.c_double * nrhs)(*[float(v) for v in bv])
+        _check(_lib.hr_axpby(self._h, _ptr(x), _ptr(y), A, B, parity, prec, nrhs), "hr_axpby")
 
     def cg_solve(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
                  inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,

@@ -68,3 +68,72 @@ class SlabDirac:
             exchange_faces(su, sd, ru, rd, self.group)
             s.domain_hop_end(o, op, m0, self.prec, stage, ru, rd, nrhs=self.nrhs, dagger=dagger)
         return out
+
+
+def global_sum(values, group=None, device=None):
+    """Sum per-rank FP64 scalars over the ranks of the group: one all-reduce of
+    the whole list (the only collective of a CG iteration besides the faces)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(t, group=group)
+    return t.tolist()
+
+
+def slab_cg(sd: SlabDirac, x, b, parity: int, m0: float, tol: float, maxit: int = 10000, group=None,
+            device=None):
+    """Conjugate gradient (Sec. 3.3) on Dhat_p^+ Dhat_p x = b over the slabs of
+    all ranks of the group, x0 = 0.
+
+    ``x`` and ``b`` are this rank's internal fields (parity p, the precision and
+    right-hand sides of ``sd``).  Every operator application exchanges the slab
+    faces (SlabDirac); every global scalar -- |b|^2, <p, M p> = |Dhat p|^2 and
+    |r|^2 -- is this rank's partial sum all-reduced in FP64 over the group
+    (``device``: where the reduction tensor lives, e.g. the GPU for NCCL).  The
+    vector updates run on the slab (``axpby``, in libhr for a GPU slab).
+    Stopping rule as the library's CG: the recursive |r| <= tol |b| per rhs,
+    then the true residual b - M x (restart from it if it is still above).
+    Returns (iterations, true relative residual per rhs)."""
+    s, prec, nr = sd.slab, sd.prec, sd.nrhs
+    r = s.new_field(parity, prec, nr)
+    p = s.new_field(parity, prec, nr)
+    t = s.new_field(parity, prec, nr)
+    Mp = s.new_field(parity, prec, nr)
+    ones, zeros = [1.0] * nr, [0.0] * nr
+    s.axpby(b, x, zeros, zeros, parity, prec, nr)     # x = 0
+    s.axpby(b, r, ones, zeros, parity, prec, nr)      # r = b
+    s.axpby(b, p, ones, zeros, parity, prec, nr)      # p = b
+    bb = global_sum(s.norm2(b, parity, prec, nr), group, device)
+    stop = [tol * tol * v for v in bb]
+    rr = list(bb)
+
+    def apply_M(out, inp):
+        sd.apply(t, inp, parity, m0)
+        sd.apply(out, t, parity, m0, dagger=True)
+
+    it = 0
+    while it < maxit:
+        active = [rr[k] > stop[k] for k in range(nr)]
+        sd.apply(t, p, parity, m0)
+        pAp = global_sum(s.norm2(t, parity, prec, nr), group, device)
+        sd.apply(Mp, t, parity, m0, dagger=True)
+        alpha = [rr[k] / pAp[k] if active[k] and pAp[k] > 0 else 0.0 for k in range(nr)]
+        s.axpby(p, x, alpha, ones, parity, prec, nr)
+        s.axpby(Mp, r, [-a for a in alpha], ones, parity, prec, nr)
+        rr_new = global_sum(s.norm2(r, parity, prec, nr), group, device)
+        it += 1
+        if all(rr_new[k] <= stop[k] for k in range(nr)):
+            apply_M(Mp, x)                                 # true residual r = b - M x
+            s.axpby(b, r, ones, zeros, parity, prec, nr)
+            s.axpby(Mp, r, [-1.0] * nr, ones, parity, prec, nr)
+            rt = global_sum(s.norm2(r, parity, prec, nr), group, device)
+            if all(rt[k] <= stop[k] for k in range(nr)):
+                return it, [(rt[k] / bb[k]) ** 0.5 if bb[k] > 0 else 0.0 for k in range(nr)]
+            s.axpby(r, p, ones, zeros, parity, prec, nr)   # restart from the true residual
+            rr = rt
+            continue
+        beta = [rr_new[k] / rr[k] if active[k] else 1.0 for k in range(nr)]
+        s.axpby(r, p, [1.0 if active[k] else 0.0 for k in range(nr)], beta, parity, prec, nr)
+        rr = rr_new
+    raise RuntimeError(f"slab_cg: no convergence in {maxit} iterations")

@@ -1,5 +1,6 @@
 """A host-side stand-in for one time slab of libhr (test infrastructure): the
-same begin / end contract as ``hr.Lattice.domain_hop_begin`` / ``_end``,
+same begin / end contract as ``hr.Lattice.domain_hop_begin`` / ``_end`` (and
+the ``norm2`` / ``axpby`` of ``hr.Lattice``, over this slab's sites),
 computed with numpy on full 4-spinors from the oracle's conventions, so that
 ``paper_2405_19294_gb300.slabs`` (buffer routing, stage order, exchange over
 a process group) can run on gloo ranks without a GPU.  Its face buffers hold
@@ -28,6 +29,15 @@ class FakeSlab:
     # fields: complex128 [nrhs, V_loc, 4, d] CPU tensors; only sites of their parity are used
     def new_field(self, parity, prec, nrhs=1):
         return torch.zeros((nrhs, self.geom.V, 4, self.d), dtype=torch.complex128)
+
+    def norm2(self, x, parity, prec, nrhs=1):
+        m = self.geom.parity == parity
+        return [float(np.sum(np.abs(x[r].numpy()[m]) ** 2)) for r in range(nrhs)]
+
+    def axpby(self, x, y, a, b, parity, prec, nrhs=1):
+        m = torch.from_numpy(self.geom.parity == parity)
+        for r in range(nrhs):
+            y[r][m] = a[r] * x[r][m] + b[r] * y[r][m]
 
     def new_halo(self, prec, nrhs=1):
         return torch.zeros((nrhs, self.L ** 3, 4, self.d), dtype=torch.complex128)

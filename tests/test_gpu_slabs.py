@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from gpu_helpers import TOL, from_complex, oracle_operator, rel_err, to_complex
+from oracle.dirac import Geometry
 from paper_2405_19294_gb300 import inputs, slabs
 
 pytestmark = pytest.mark.gpu
@@ -112,3 +113,52 @@ def test_slab_errors(hr):
     U = torch.zeros((lat.V, 4, 3, 3, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(hr.HrError):
         lat.represent_links(U, False, 1.0)                  # clover on a slab
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_axpby(hr, prec):
+    """hr_axpby: y = a x + b y per rhs, against NumPy on the unpacked fields."""
+    T, L, N, rep = 4, 4, 3, "sym"
+    lat = _slabs(hr, T, L, N, rep, 1)[0]
+    psi = inputs.gaussian_spinor(7, T, L, lat.d, nrhs=3)
+    phi = inputs.gaussian_spinor(8, T, L, lat.d, nrhs=3)
+    x, y = lat.new_field(0, prec, 3), lat.new_field(0, prec, 3)
+    lat.pack(x, from_complex(psi), 0, prec, 3)
+    lat.pack(y, from_complex(phi), 0, prec, 3)
+
+    def back(f):
+        out = torch.zeros((3, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+        lat.unpack(out, f, 0, prec, 3)
+        return to_complex(out)
+    xs, ys = back(x), back(y)
+    a, b = [0.5, -2.0, 0.0], [1.5, 0.25, 0.0]
+    lat.axpby(x, y, a, b, 0, prec, 3)
+    got = back(y)
+    ev = Geometry(T, L).parity == 0
+    for r in range(3):
+        ref = a[r] * xs[r] + b[r] * ys[r]
+        if r == 2:
+            assert np.all(got[r][ev] == 0)
+        else:
+            assert rel_err(got[r], ref, ev) < {0: 1e-15, 1: 1e-7, 2: 1e-3}[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_slab_cg_on_one_slab(hr, prec):
+    """slabs.slab_cg driving libhr (hr_axpby, hr_norm2, the slab hops) on one slab
+    that spans the lattice: FP64 true residual of the oracle's operator <= 1e-10
+    (FP64 fields), or the FP32 floor (FP32 fields)."""
+    T, L, N, rep, m0 = 8, 4, 3, "fund", -0.3
+    lat = _slabs(hr, T, L, N, rep, 1)[0]
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    ev = op.geom.parity == 0
+    b = np.where(ev[:, None, None], inputs.gaussian_spinor(9, T, L, lat.d)[0], 0)
+    fb = _pack(lat, b[None], 0, prec)
+    fx = lat.new_field(0, prec)
+    sd = slabs.SlabDirac(lat, prec)
+    tol = 1e-10 if prec == 0 else 1e-4
+    it, res = slabs.slab_cg(sd, fx, fb, 0, m0, tol)
+    x = _unpack(lat, fx, 0, prec)
+    r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
+    true = np.linalg.norm(r) / np.linalg.norm(b)
+    assert res[0] <= tol and true <= (1.05e-10 if prec == 0 else 2e-4), (it, res, true)
