@@ -117,6 +117,9 @@ struct hr_batch {
   std::vector<BClass> cls;
   cudaStream_t stream;  // caller's stream
   cudaStream_t s;       // internal stream (capturable)
+  std::vector<cudaStream_t> cs;  // one per class: the classes of a hopping stage run concurrently
+  std::vector<cudaEvent_t> cev;  // per class: its launch of the stage is done
+  cudaEvent_t fork;              // the stage may start
   HopK *d_desc;         // [8 stages][n]: inner Dhat, inner Dhat^+, FP64 Dhat, FP64 Dhat^+
   HopK *h_desc;         // pinned staging
   BPair *d_pairs;       // [B_NPAIRS][n] operand pairs of the batched axpby
@@ -206,6 +209,22 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
     }
   };
   A(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+  // the classes run largest first (by even sites x link reals), each on its own stream
+  std::sort(b->cls.begin(), b->cls.end(), [&](const BClass &x, const BClass &y) {
+    auto work = [&](const BClass &c) {
+      double w = 0.0;
+      for (int li : c.members) w += (double)lats[li]->Vh;
+      return w * (c.is_real ? 1.0 : 2.0) * c.d * c.d;
+    };
+    return work(x) > work(y);
+  });
+  b->cs.assign(b->cls.size(), nullptr);
+  b->cev.assign(b->cls.size(), nullptr);
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    A(cudaStreamCreateWithFlags(&b->cs[c], cudaStreamNonBlocking));
+    A(cudaEventCreateWithFlags(&b->cev[c], cudaEventDisableTiming));
+  }
+  A(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   A(cudaMalloc(&b->d_desc, sizeof(HopK) * 8 * n));
   A(cudaMallocHost(&b->h_desc, sizeof(HopK) * 8 * n));
   A(cudaMalloc(&b->d_pairs, sizeof(BPair) * B_NPAIRS * n));
@@ -241,6 +260,14 @@ extern "C" int hr_batch_destroy(hr_batch *b) {
     cudaStreamSynchronize(b->s);
     cudaStreamDestroy(b->s);
   }
+  for (auto st : b->cs)
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (auto e : b->cev)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (auto &c : b->cls)
     for (int q = 0; q < 3; ++q) cudaFree(c.items[q]);
   cudaFree(b->d_desc);
@@ -357,11 +384,27 @@ extern "C" int hr_batch_set_shape(hr_batch *b, int d, int is_real, int prec, int
   return HR_ERR_ARG;
 }
 
+// One hopping stage (descriptor slot `slot`) of every class: the class
+// launches fork from `s` onto the classes' own streams and join back, so the
+// small classes run beside the large ones instead of after them (inside a
+// captured graph these become parallel branches).
+static int batch_stage(hr_batch *b, int prec, int slot, const int *frozen, cudaStream_t s) {
+  const HopK *descs = b->d_desc + (size_t)slot * b->n;
+  if (b->cls.size() == 1) return launch_multi(prec, b->cls[0], descs, frozen, s);
+  HR_CUDA(cudaEventRecord(b->fork, s));
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    HR_CUDA(cudaStreamWaitEvent(b->cs[c], b->fork, 0));
+    HR_TRY(launch_multi(prec, b->cls[c], descs, frozen, b->cs[c]));
+    HR_CUDA(cudaEventRecord(b->cev[c], b->cs[c]));
+  }
+  for (size_t c = 0; c < b->cls.size(); ++c) HR_CUDA(cudaStreamWaitEvent(s, b->cev[c], 0));
+  return HR_OK;
+}
+
 // launches of one batched Dhat (stages slot0, slot0+1 of d_desc)
 static int batch_dhat(hr_batch *b, int prec, int slot0, const int *frozen, cudaStream_t s) {
-  for (const auto &c : b->cls) HR_TRY(launch_multi(prec, c, b->d_desc + (size_t)slot0 * b->n, frozen, s));
-  for (const auto &c : b->cls) HR_TRY(launch_multi(prec, c, b->d_desc + (size_t)(slot0 + 1) * b->n, frozen, s));
-  return HR_OK;
+  HR_TRY(batch_stage(b, prec, slot0, frozen, s));
+  return batch_stage(b, prec, slot0 + 1, frozen, s);
 }
 
 extern "C" int hr_batch_dphi(hr_batch *b, void *const *out, const void *const *in, int parity, const double *m0,

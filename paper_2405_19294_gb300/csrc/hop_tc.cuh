@@ -28,19 +28,22 @@
 //   C lane (g, t) = colour g, columns 2t, 2t+1 = rows h0, h1 of rhs t,
 //   so each lane rebuilds the four spin rows of (colour g, rhs t) from its
 //   own accumulator registers.
-// Lane (g, t) loads the neighbour components its B fragment needs -- colours
-// t and t+4 (TF32) or 2t and 2t+1 (FP16) of one rhs, the two spin components
-// of its half-spinor row only -- straight from global memory.
 //
 // Work split.  A block covers S = 16 consecutive output sites x R <= 16 rhs.
-//   1. The links of all 8 hops of the S sites (row-major per site, so a warp
+//   0. The links of all 8 hops of the S sites (row-major per site, so a warp
 //      reads one site's matrix from one shared-memory row) and, with clover,
 //      the packed A or A^{-1} blocks are staged by cp.async.
-//   2. Each warp takes the sites of the tile in turn and runs the 8 hops of
-//      one site with its sums in registers (4 rhs tiles x 4 spin rows).
-//   3. The sums go through shared memory to one thread per (site, rhs), which
-//      runs the epilogue of the multi-rhs kernel (scaling, clover, self term,
-//      store).
+//   Then, hop by hop (double-buffered, one barrier per hop):
+//   1. one thread per (site, rhs) loads the neighbour spinor of the next hop
+//      (coalesced: consecutive threads read consecutive sites), projects it
+//      and writes the two half-spinor rows to shared memory in B-fragment
+//      order;
+//   2. each warp runs the MMA tiles of its (site, 4-rhs tile) units of the
+//      current hop from shared memory and rebuilds the spin rows into its
+//      accumulator registers.
+//   3. After the last hop the sums go through shared memory to one thread per
+//      (site, rhs), which runs the epilogue of the multi-rhs kernel (scaling,
+//      clover, self term, store).
 #pragma once
 
 #include "hop_mrhs.cuh"
@@ -50,7 +53,7 @@ namespace tc {
 constexpr int S = 16;        // output sites per block
 constexpr int NT = 256;      // threads per block
 constexpr int NW = NT / 32;  // warps per block
-constexpr int RMAX = 16;     // right-hand sides per block
+constexpr int RMAX = 12;     // right-hand sides per block (three 4-rhs MMA tiles)
 constexpr int RS = S + 1;    // sum staging: float2 stride between rhs (odd: conflict-free)
 
 __device__ __forceinline__ unsigned f2tf32(float x) {
@@ -88,35 +91,87 @@ __device__ __forceinline__ int partner_spin(int hh) { return (MU == 0 || MU == 3
 template <int MU>
 __device__ __forceinline__ float partner_sign(int hh, float sig) { return (MU <= 1 || hh == 0) ? -sig : sig; }
 
-// FP32 field: spin s of colour c sits in chunk 2c + s/2, half s%2 (float2)
-template <int MU>
-__device__ __forceinline__ cx<float> proj_f32(const char *f, int64_t Vh, int64_t j, int c, int hh, float fs) {
-  const int k = partner_spin<MU>(hh);
-  const float2 a = __ldg(reinterpret_cast<const float2 *>(f + (((int64_t)(2 * c) * Vh + j) << 4)) + hh);
-  const float2 b = __ldg(reinterpret_cast<const float2 *>(f + (((int64_t)(2 * c + 1) * Vh + j) << 4)) + (k & 1));
-  if (MU == 0 || MU == 2) return mk(fmaf(fs, b.x, a.x), fmaf(fs, b.y, a.y));
-  return mk(fmaf(-fs, b.y, a.x), fmaf(fs, b.x, a.y));  // a + i fs b
+// ------------------------------------------------------------------------
+// Phase 1: one thread per (site, rhs) loads the neighbour spinor of one hop
+// (coalesced: consecutive threads read consecutive sites), projects it to the
+// two half-spinor rows and writes them to shared memory as MMA B operands.
+// B row layout (one row per fragment column n = 2 rhs + half-spinor row, RW
+// 32-bit words; RW = 12 = 4 mod 8 keeps the 8 rows x 4 words of one fragment
+// load on distinct banks):
+//   FP32: Re h_0 .. Re h_{D-1}, Im h_0 .. Im h_{D-1}            (floats)
+//   FP16: (Re h_0, Re h_1), (Re h_2, Re h_3), ... in words 0..3,
+//         (Im h_0, Im h_1), ... in words 4..7                   (half2)
+// Rows of one site are NCOL = 32 apart plus a pad of 4 words, so the 16 sites
+// written by one warp spread over the banks.  Colours >= D (and the rhs
+// beyond the block's) stay zero from the initial clear.
+constexpr int RW = 12;                 // words per B row
+constexpr int NCOL = 2 * RMAX;         // B rows (fragment columns) per site
+constexpr int SSTR = NCOL * RW + 4;    // words per site
+constexpr int BBUF = S * SSTR;         // words per buffer
+
+// The neighbour spinor of one (site, rhs) as loaded for phase 1: 2D float4
+// chunks (FP32) or D uint4 chunks (FP16).  Loading is split from projecting so
+// that the loads of the next hop are in flight while the warp runs the MMA
+// tiles of the current one.
+template <int D, int P>
+struct Nb {
+  uint4 v[P == 1 ? 2 * D : D];
+};
+template <int D, int P>
+__device__ __forceinline__ void nb_load(Nb<D, P> &nb, const char *f, int64_t Vh, int64_t j) {
+  const uint4 *b = reinterpret_cast<const uint4 *>(f);
+#pragma unroll
+  for (int c = 0; c < (P == 1 ? 2 * D : D); ++c) nb.v[c] = __ldg(b + (int64_t)c * Vh + j);
+}
+template <int D, int P, int MU>
+__device__ __forceinline__ void project_store(const Nb<D, P> &nb, float sig, uint32_t *row0, uint32_t *row1) {
+  if constexpr (P == 1) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const uint4 a = nb.v[2 * c], b = nb.v[2 * c + 1];
+      cx<float> psi[4], h0, h1;
+      psi[0] = mk(__uint_as_float(a.x), __uint_as_float(a.y));
+      psi[1] = mk(__uint_as_float(a.z), __uint_as_float(a.w));
+      psi[2] = mk(__uint_as_float(b.x), __uint_as_float(b.y));
+      psi[3] = mk(__uint_as_float(b.z), __uint_as_float(b.w));
+      project<MU>(sig, psi, h0, h1);
+      row0[c] = __float_as_uint(h0.x);
+      row0[D + c] = __float_as_uint(h0.y);
+      row1[c] = __float_as_uint(h1.x);
+      row1[D + c] = __float_as_uint(h1.y);
+    }
+  } else {
+    unsigned h0[D], h1[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) project_h2<MU>(sig, nb.v[c], h0[c], h1[c]);
+    unsigned w0[8], w1[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 2 * q;
+      const __half2 z = __float2half2_rn(0.f);
+      const __half2 a0 = (c < D) ? u2h(h0[c < D ? c : 0]) : z, b0 = (c + 1 < D) ? u2h(h0[c + 1 < D ? c + 1 : 0]) : z;
+      const __half2 a1 = (c < D) ? u2h(h1[c < D ? c : 0]) : z, b1 = (c + 1 < D) ? u2h(h1[c + 1 < D ? c + 1 : 0]) : z;
+      w0[q] = h2u(__lows2half2(a0, b0));
+      w0[4 + q] = h2u(__highs2half2(a0, b0));
+      w1[q] = h2u(__lows2half2(a1, b1));
+      w1[4 + q] = h2u(__highs2half2(a1, b1));
+    }
+    reinterpret_cast<uint4 *>(row0)[0] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    reinterpret_cast<uint4 *>(row0)[1] = make_uint4(w0[4], w0[5], w0[6], w0[7]);
+    reinterpret_cast<uint4 *>(row1)[0] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    reinterpret_cast<uint4 *>(row1)[1] = make_uint4(w1[4], w1[5], w1[6], w1[7]);
+  }
 }
 
-// FP16 field: colour c is one 16-byte chunk of the four spins (half2 each);
-// the row is formed in half2 arithmetic (one rounding, as the site kernel)
-template <int MU>
-__device__ __forceinline__ __half2 proj_f16(const char *f, int64_t Vh, int64_t j, int c, int hh, float fs) {
-  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(f) + (int64_t)c * Vh + j);
-  const int k = partner_spin<MU>(hh);
-  const unsigned a = hh ? v.y : v.x;
-  const unsigned b = (k == 2) ? v.z : v.w;
-  if (MU == 0 || MU == 2) return __hfma2(__float2half2_rn(fs), u2h(b), u2h(a));
-  return __hfma2(__floats2half2_rn(-fs, fs), __lowhigh2highlow(u2h(b)), u2h(a));
-}
-
-// One hop of one site for every rhs tile of the block, FP32 fields (3xTF32).
-// lrow: the staged link matrix (row-major, d*d float2) of this hop;
-// acc[k][r]: spin row r of (colour g, rhs 4k + t).
-template <int D, int MU, bool ADJ>
-__device__ __forceinline__ void hop_f32(cx<float> (&acc)[4][4], const char *in, size_t stride, int64_t Vh,
-                                        int64_t j, const float2 *lrow, float sig, int g, int t, int ntile,
-                                        int nr) {
+// Phase 2, one fragment tile (4 rhs) of one site and hop, FP32 (3xTF32):
+// A from the link matrix (precomputed big / small parts), B from the rows
+// 8k .. 8k+7 of the site, then the rebuild of the four spin rows of
+// (colour g, rhs 4k + t).
+struct AF32 {
+  unsigned xb1, xs1, yb1, ys1, xb2, xs2, yb2, ys2;
+};
+template <int D, bool ADJ>
+__device__ __forceinline__ AF32 a_f32(const float2 *lrow, int g, int t) {
   float2 u1 = make_float2(0.f, 0.f), u2 = u1;
   if (g < D) {
     if (t < D) u1 = lrow[ADJ ? t * D + g : g * D + t];
@@ -126,46 +181,46 @@ __device__ __forceinline__ void hop_f32(cx<float> (&acc)[4][4], const char *in, 
     u1.y = -u1.y;
     u2.y = -u2.y;
   }
-  // k-step 0 (Re h columns): (Re u1, Im u1, Re u2, Im u2); k-step 1 (Im h): (-Im u1, Re u1, -Im u2, Re u2)
-  unsigned xb1, xs1, yb1, ys1, xb2, xs2, yb2, ys2;
-  split_tf32(u1.x, xb1, xs1);
-  split_tf32(u1.y, yb1, ys1);
-  split_tf32(u2.x, xb2, xs2);
-  split_tf32(u2.y, yb2, ys2);
+  AF32 a;
+  split_tf32(u1.x, a.xb1, a.xs1);
+  split_tf32(u1.y, a.yb1, a.ys1);
+  split_tf32(u2.x, a.xb2, a.xs2);
+  split_tf32(u2.y, a.yb2, a.ys2);
+  return a;
+}
+template <int D, int MU>
+__device__ __forceinline__ void tile_f32(cx<float> (&acc)[4], const AF32 &a, const uint32_t *rows, float sig, int g,
+                                         int t) {
+  // k-step 0 (Re h columns): A = (Re u1, Im u1, Re u2, Im u2), B = (Re h_t, Re h_t+4);
+  // k-step 1 (Im h columns): A = (-Im u1, Re u1, -Im u2, Re u2), B = (Im h_t, Im h_t+4)
+  const uint32_t *row = rows + g * RW;
+  const float r1 = (t < D) ? __uint_as_float(row[t]) : 0.f;
+  const float r2 = (t + 4 < D) ? __uint_as_float(row[t + 4]) : 0.f;
+  const float i1 = (t < D) ? __uint_as_float(row[D + t]) : 0.f;
+  const float i2 = (t + 4 < D) ? __uint_as_float(row[D + t + 4]) : 0.f;
+  unsigned rb1, rs1, rb2, rs2, ib1, is1, ib2, is2;
+  split_tf32(r1, rb1, rs1);
+  split_tf32(r2, rb2, rs2);
+  split_tf32(i1, ib1, is1);
+  split_tf32(i2, ib2, is2);
   const unsigned SB = 0x80000000u;  // sign flip (exact on TF32)
-  const int hh = g & 1;
-  const float fs = partner_sign<MU>(hh, sig);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (k >= ntile) break;
-    const int rb = 4 * k + (g >> 1);
-    cx<float> h1 = mk(0.f, 0.f), h2 = h1;
-    if (rb < nr) {
-      const char *f = in + (size_t)rb * stride;
-      if (t < D) h1 = proj_f32<MU>(f, Vh, j, t, hh, fs);
-      if (t + 4 < D) h2 = proj_f32<MU>(f, Vh, j, t + 4, hh, fs);
-    }
-    unsigned rb1, rs1, rb2, rs2, ib1, is1, ib2, is2;
-    split_tf32(h1.x, rb1, rs1);
-    split_tf32(h2.x, rb2, rs2);
-    split_tf32(h1.y, ib1, is1);
-    split_tf32(h2.y, ib2, is2);
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_tf32(c, xs1, ys1, xs2, ys2, rb1, rb2);
-    mma_tf32(c, xb1, yb1, xb2, yb2, rs1, rs2);
-    mma_tf32(c, ys1 ^ SB, xs1, ys2 ^ SB, xs2, ib1, ib2);
-    mma_tf32(c, yb1 ^ SB, xb1, yb2 ^ SB, xb2, is1, is2);
-    mma_tf32(c, xb1, yb1, xb2, yb2, rb1, rb2);
-    mma_tf32(c, yb1 ^ SB, xb1, yb2 ^ SB, xb2, ib1, ib2);
-    reconstruct<MU>(sig, mk(c[0], c[2]), mk(c[1], c[3]), acc[k]);
-  }
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  mma_tf32(c, a.xs1, a.ys1, a.xs2, a.ys2, rb1, rb2);
+  mma_tf32(c, a.xb1, a.yb1, a.xb2, a.yb2, rs1, rs2);
+  mma_tf32(c, a.ys1 ^ SB, a.xs1, a.ys2 ^ SB, a.xs2, ib1, ib2);
+  mma_tf32(c, a.yb1 ^ SB, a.xb1, a.yb2 ^ SB, a.xb2, is1, is2);
+  mma_tf32(c, a.xb1, a.yb1, a.xb2, a.yb2, rb1, rb2);
+  mma_tf32(c, a.yb1 ^ SB, a.xb1, a.yb2 ^ SB, a.xb2, ib1, ib2);
+  reconstruct<MU>(sig, mk(c[0], c[2]), mk(c[1], c[3]), acc);
 }
 
-// The same for FP16 fields (one m16n8k16 tile per 4 rhs).
-template <int D, int MU, bool ADJ>
-__device__ __forceinline__ void hop_f16(cx<float> (&acc)[4][4], const char *in, size_t stride, int64_t Vh,
-                                        int64_t j, const __half2 *lrow, float sig, int g, int t, int ntile,
-                                        int nr) {
+// The same for FP16 fields (one m16n8k16 tile; w = the neighbour's site scale
+// of the accumulator's rhs)
+struct AF16 {
+  unsigned ar, ai, an;
+};
+template <int D, bool ADJ>
+__device__ __forceinline__ AF16 a_f16(const __half2 *lrow, int g, int t) {
   const __half2 z = __float2half2_rn(0.f);
   __half2 u1 = z, u2 = z;
   if (g < D) {
@@ -173,41 +228,44 @@ __device__ __forceinline__ void hop_f16(cx<float> (&acc)[4][4], const char *in, 
     if (2 * t + 1 < D) u2 = lrow[ADJ ? (2 * t + 1) * D + g : g * D + 2 * t + 1];
   }
   // rows g (Re out) and g+8 (Im out) against columns 2t, 2t+1 (Re in) and 2t+8, 2t+9 (Im in)
-  const unsigned ar = h2u(__lows2half2(u1, u2));
   __half2 ai = __highs2half2(u1, u2);
   if (ADJ) ai = __hneg2(ai);
-  const unsigned aiu = h2u(ai), ain = h2u(__hneg2(ai));
-  const int hh = g & 1;
-  const float fs = partner_sign<MU>(hh, sig);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (k >= ntile) break;
-    const int rb = 4 * k + (g >> 1);
-    __half2 h1 = z, h2 = z;
-    if (rb < nr) {
-      const char *f = in + (size_t)rb * stride;
-      if (2 * t < D) h1 = proj_f16<MU>(f, Vh, j, 2 * t, hh, fs);
-      if (2 * t + 1 < D) h2 = proj_f16<MU>(f, Vh, j, 2 * t + 1, hh, fs);
-    }
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_f16(c, ar, aiu, ain, ar, h2u(__lows2half2(h1, h2)), h2u(__highs2half2(h1, h2)));
-    const int rd = 4 * k + t;  // the rhs this lane's accumulator columns belong to
-    const float w = (rd < nr) ? f16_scales(in + (size_t)rd * stride, Vh, D)[j] : 0.f;
-    reconstruct_w<MU>(sig, w, mk(c[0], c[2]), mk(c[1], c[3]), acc[k]);
-  }
+  AF16 a;
+  a.ar = h2u(__lows2half2(u1, u2));
+  a.ai = h2u(ai);
+  a.an = h2u(__hneg2(ai));
+  return a;
+}
+template <int MU>
+__device__ __forceinline__ void tile_f16(cx<float> (&acc)[4], const AF16 &a, const uint32_t *rows, float w, float sig,
+                                         int g, int t) {
+  const uint32_t *row = rows + g * RW;
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  mma_f16(c, a.ar, a.ai, a.an, a.ar, row[t], row[4 + t]);
+  reconstruct_w<MU>(sig, w, mk(c[0], c[2]), mk(c[1], c[3]), acc);
 }
 
-// bytes of the dynamic shared memory of one block: staged links, staged sums
-// (4D x es float2), clover blocks, neighbour indices
+// bytes of the dynamic shared memory of one block
 template <int D, int P, bool CLOVER>
 struct Smem {
   static constexpr int NCH = D * D;
   static constexpr int ES = (P == 1) ? 8 : 4;  // staged link chunk (float2 / half2)
   static constexpr int LST = NCH | 1;          // chunks per staged link row (odd: conflict-free fill)
   static constexpr size_t LINKS = ((size_t)8 * S * LST * ES + 15) & ~(size_t)15;
+  static constexpr size_t BROWS = (size_t)2 * BBUF * 4;       // two B buffers
+  static constexpr size_t WSC = (size_t)2 * S * RMAX * 4;    // FP16 site scales per buffer
   static constexpr size_t CLOV = CLOVER ? (size_t)4 * D * D * S * 8 : 0;
   static constexpr size_t NBI = (size_t)8 * S * sizeof(int64_t);
-  static size_t bytes(int es) { return LINKS + (size_t)4 * D * es * 8 + CLOV + NBI; }
+  // the staged sums (4D x es float2) reuse the link and B-row space after the last hop
+  __host__ __device__ static size_t bytes(int es) {
+    const size_t sums = (size_t)4 * D * es * 8;
+    const size_t work = LINKS + BROWS > sums ? LINKS + BROWS : sums;
+    return work + WSC + CLOV + NBI;
+  }
+  __host__ __device__ static size_t work(int es) {
+    const size_t sums = (size_t)4 * D * es * 8;
+    return LINKS + BROWS > sums ? LINKS + BROWS : sums;
+  }
 };
 
 // float2 stride between the spin/colour rows of the staged sums: >= R * RS and
@@ -223,8 +281,10 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
   typedef Smem<D, P, CLOVER> M;
   extern __shared__ __align__(16) char smem[];
   char *lsm = smem;
-  float2 *sums = reinterpret_cast<float2 *>(smem + M::LINKS);
-  char *cbuf = smem + M::LINKS + (size_t)4 * D * es * 8;
+  uint32_t *brows = reinterpret_cast<uint32_t *>(smem + M::LINKS);
+  float2 *sums = reinterpret_cast<float2 *>(smem);  // after the last hop
+  float *wsc = reinterpret_cast<float *>(smem + M::work(es));
+  char *cbuf = smem + M::work(es) + M::WSC;
   int64_t *nbi = reinterpret_cast<int64_t *>(cbuf + M::CLOV);  // [8][S]
 
   const int nrb = (k.nrhs + R - 1) / R;
@@ -257,6 +317,9 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
     nbi[6 * S + s] = ii + (int64_t)(zf - st.z) * LLh;
     nbi[7 * S + s] = ii + (int64_t)(zb - st.z) * LLh;
   }
+  for (int w = threadIdx.x; w < 2 * BBUF; w += NT) brows[w] = 0u;  // pads and unused rhs stay zero
+  if (P == 2)
+    for (int w = threadIdx.x; w < 2 * S * RMAX; w += NT) wsc[w] = 0.f;
   __syncthreads();
   // stage the links of the 8 hops: hop n = 2 mu + back; forward: slot [p][mu] at
   // the output site, backward: slot [1-p][mu] at the backward neighbour
@@ -281,51 +344,108 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
     }
     cp_async_commit();
   }
-  cp_async_wait<1>();  // the links are in (the clover may still be streaming)
-  __syncthreads();
 
+  // phase 1 item of this thread: site ps, rhs pq of the block
+  const int ps = threadIdx.x % S, pq = threadIdx.x / S;
+  const bool p1 = (pq < nr) && (i0 + ps < Vh);
+  const char *pin = reinterpret_cast<const char *>(k.in) + (size_t)(rbase + (pq < nr ? pq : 0)) * k.stride;
+  const float sg = (float)k.sgn;
+  Nb<D, P> nb;
+  float nbw = 0.f;  // FP16: the neighbour's site scale
+  auto p1_load = [&](int n) {
+    if (!p1) return;
+    const int64_t j = nbi[n * S + ps];
+    nb_load<D, P>(nb, pin, Vh, j);
+    if (P == 2) nbw = f16_scales(pin, Vh, D)[j];
+  };
+  auto p1_store = [&](int n, int buf) {
+    if (!p1) return;
+    const float sig = (n & 1) ? sg : -sg;
+    uint32_t *r0 = brows + buf * BBUF + ps * SSTR + (2 * pq) * RW;
+    switch (n >> 1) {
+      case 0: project_store<D, P, 0>(nb, sig, r0, r0 + RW); break;
+      case 1: project_store<D, P, 1>(nb, sig, r0, r0 + RW); break;
+      case 2: project_store<D, P, 2>(nb, sig, r0, r0 + RW); break;
+      default: project_store<D, P, 3>(nb, sig, r0, r0 + RW); break;
+    }
+    if (P == 2) wsc[buf * S * RMAX + ps * RMAX + pq] = nbw;
+  };
+
+  // phase 2: warp w owns sites 2w, 2w+1 of the tile and all NTILE 4-rhs tiles of
+  // each (tiles beyond the block's rhs multiply zero rows; sites beyond V/2
+  // compute on the rows of site 0 and are never stored)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int ntile = (nr + 3) >> 2;
-  const char *in = reinterpret_cast<const char *>(k.in) + (size_t)rbase * k.stride;
-  const float sg = (float)k.sgn;
-  for (int s = warp; s < S; s += NW) {
-    if (i0 + s >= Vh) break;  // warp-uniform
-    cx<float> acc[4][4];
+  constexpr int NTILE = RMAX / 4;
+  constexpr int SPW = S / NW;  // sites per warp
+  cx<float> acc[SPW][NTILE][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+  for (int a = 0; a < SPW; ++a)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[q][r] = mk(0.f, 0.f);
+    for (int q = 0; q < NTILE; ++q)
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const int64_t j = nbi[n * S + s];
-      const char *lrow = lsm + (size_t)(n * S + s) * M::LST * M::ES;
-      const float sig = (n & 1) ? sg : -sg;
-#define HR_TC_HOP(MU, ADJ)                                                                                    \
-  if (P == 1)                                                                                                 \
-    hop_f32<D, MU, ADJ>(acc, in, k.stride, Vh, j, reinterpret_cast<const float2 *>(lrow), sig, g, t, ntile, nr); \
-  else                                                                                                        \
-    hop_f16<D, MU, ADJ>(acc, in, k.stride, Vh, j, reinterpret_cast<const __half2 *>(lrow), sig, g, t, ntile, nr);
-      switch (n) {
-        case 0: HR_TC_HOP(0, false) break;
-        case 1: HR_TC_HOP(0, true) break;
-        case 2: HR_TC_HOP(1, false) break;
-        case 3: HR_TC_HOP(1, true) break;
-        case 4: HR_TC_HOP(2, false) break;
-        case 5: HR_TC_HOP(2, true) break;
-        case 6: HR_TC_HOP(3, false) break;
-        default: HR_TC_HOP(3, true) break;
-      }
-#undef HR_TC_HOP
+      for (int r = 0; r < 4; ++r) acc[a][q][r] = mk(0.f, 0.f);
+
+  p1_load(0);
+  p1_store(0, 0);
+  cp_async_wait<1>();  // the links are in (the clover may still be streaming)
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    __syncthreads();  // hop n's B rows are written; hop n-1's are no longer read
+    if (n < 7) {  // FP16: the loads stay in flight during the MMA tiles of hop n
+      p1_load(n + 1);
+      if (P == 1) p1_store(n + 1, (n + 1) & 1);  // FP32: too many registers to hold them
     }
-    if (g < D) {
+    const uint32_t *bb = brows + (n & 1) * BBUF;
+    const float sig = (n & 1) ? sg : -sg;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+    for (int a = 0; a < SPW; ++a) {
+      const int s = SPW * warp + a;
+      const char *lrow = lsm + (size_t)(n * S + s) * M::LST * M::ES;
+      const uint32_t *rows = bb + s * SSTR;
+#define HR_TC_SITE(MU, ADJ)                                                                               \
+  if (P == 1) {                                                                                           \
+    const AF32 af = a_f32<D, ADJ>(reinterpret_cast<const float2 *>(lrow), g, t);                          \
+    _Pragma("unroll") for (int q = 0; q < NTILE; ++q)                                                     \
+      tile_f32<D, MU>(acc[a][q], af, rows + q * 8 * RW, sig, g, t);                                       \
+  } else {                                                                                                \
+    const AF16 af = a_f16<D, ADJ>(reinterpret_cast<const __half2 *>(lrow), g, t);                         \
+    float c[NTILE][4];                                                                                    \
+    _Pragma("unroll") for (int q = 0; q < NTILE; ++q) {                                                   \
+      const uint32_t *row = rows + (q * 8 + g) * RW;                                                      \
+      c[q][0] = c[q][1] = c[q][2] = c[q][3] = 0.f;                                                        \
+      mma_f16(c[q], af.ar, af.ai, af.an, af.ar, row[t], row[4 + t]);                                      \
+    }                                                                                                     \
+    const float *w = wsc + (n & 1) * S * RMAX + s * RMAX + t;                                             \
+    _Pragma("unroll") for (int q = 0; q < NTILE; ++q)                                                     \
+      reconstruct_w<MU>(sig, w[4 * q], mk(c[q][0], c[q][2]), mk(c[q][1], c[q][3]), acc[a][q]);            \
+  }
+      switch (n) {
+        case 0: HR_TC_SITE(0, false) break;
+        case 1: HR_TC_SITE(0, true) break;
+        case 2: HR_TC_SITE(1, false) break;
+        case 3: HR_TC_SITE(1, true) break;
+        case 4: HR_TC_SITE(2, false) break;
+        case 5: HR_TC_SITE(2, true) break;
+        case 6: HR_TC_SITE(3, false) break;
+        default: HR_TC_SITE(3, true) break;
+      }
+#undef HR_TC_SITE
+    }
+    if (n < 7 && P == 2) p1_store(n + 1, (n + 1) & 1);
+  }
+  __syncthreads();  // the link and B-row space becomes the sum staging
+  if (g < D) {
+#pragma unroll
+    for (int a = 0; a < SPW; ++a) {
+      const int s = SPW * warp + a;
+#pragma unroll
+      for (int q = 0; q < NTILE; ++q) {
         const int r = 4 * q + t;
-        if (q < ntile && r < nr)
+        if (r < nr)
 #pragma unroll
           for (int sp = 0; sp < 4; ++sp)
-            sums[(size_t)(g * 4 + sp) * es + r * RS + s] = make_float2(acc[q][sp].x, acc[q][sp].y);
+            sums[(size_t)(g * 4 + sp) * es + r * RS + s] = make_float2(acc[a][q][sp].x, acc[a][q][sp].y);
       }
     }
   }

@@ -384,3 +384,4 @@ def test_tensor_core_multi_rhs(hr, N, rep, csw, prec):
                 ref = _oracle_apply(op, psi[r], parity, dagger)
                 err = rel_err(got[r], ref, mask)
                 assert err < (1e-6 if prec == 1 else 1e-3), (nrhs, parity, dagger, r, err)
+
