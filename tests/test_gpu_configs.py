@@ -119,3 +119,54 @@ def test_full_size_cg_to_1e10(hr, name):
         res = np.linalg.norm(b[sites] - Mx[sites]) / np.linalg.norm(b[sites])
         assert res < 1e-9, (name, inner, res)
         del fx
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+def test_cg_global_oracle_residual_16c32(hr, inner):
+    """Config 1's operator on 16^3 x 32 (V/2 = 65536 sites: hundreds of blocks per
+    launch): the oracle's residual |b - Dhat^+ Dhat x| / |b| over the whole lattice,
+    not only at sampled sites, meets the 1e-10 target the library reports."""
+    from gpu_helpers import gpu_lattice, oracle_operator
+    T, L, N, rep, m0 = 32, 16, 3, "fund", -0.4
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    ev = op.geom.parity == 0
+    b = np.where(ev[:, None, None], inputs.gaussian_spinor(21, T, L, lat.d)[0], 0)
+    fb = lat.new_field(0, 0)
+    lat.pack(fb, from_complex(b[None]), 0, 0)
+    fx = lat.new_field(0, 0)
+    st = lat.cg_solve(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=inner)
+    assert st["true_residual"] <= 1e-10, st
+    out = torch.zeros((1, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, fx, 0, 0)
+    lat.synchronize()
+    x = to_complex(out)[0]
+    r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
+    # the library stops on its own FP64 true residual; the oracle's evaluation differs by rounding
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10, st
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_multi_rhs_cg_global_oracle_residual(hr, inner):
+    """Config 3's operator (SU(3) sextet, clover csw = 1) on 8^3 x 16 with 12 right-hand
+    sides in one solve (FP32 or FP16 inner operator, whichever multi-rhs kernel the
+    autotuner picks), checked rhs by rhs against the oracle over the whole lattice."""
+    from gpu_helpers import gpu_lattice, oracle_operator
+    T, L, N, rep, m0, csw, nr = 16, 8, 3, "sym", -0.35, 1.0, 12
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, csw)
+    op = oracle_operator(T, L, N, rep, 1.0, m0, csw)
+    ev = op.geom.parity == 0
+    b = inputs.gaussian_spinor(22, T, L, lat.d, nr)
+    b = np.where(ev[None, :, None, None], b, 0)
+    fb = lat.new_field(0, 0, nr)
+    lat.pack(fb, from_complex(b), 0, 0, nr)
+    fx = lat.new_field(0, 0, nr)
+    st = lat.cg_solve(fx, fb, 0, m0, csw, 1e-10, inner_prec=inner, nrhs=nr)
+    assert st["true_residual"] <= 1e-10, st
+    out = torch.zeros((nr, lat.V, 4, lat.d, 2), dtype=torch.float64, device="cuda")
+    lat.unpack(out, fx, 0, 0, nr)
+    lat.synchronize()
+    x = to_complex(out)
+    for k in range(nr):
+        r = b[k] - op.apply_schur(op.apply_schur(x[k], 0), 0, dagger=True)
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1.05e-10, (k, st)
