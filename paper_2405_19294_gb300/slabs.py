@@ -25,10 +25,18 @@ from __future__ import annotations
 
 def exchange_faces(send_up, send_down, recv_up, recv_down, group=None):
     """recv_up <- send_down of the rank above; recv_down <- send_up of the rank below."""
+    import torch
     import torch.distributed as dist
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
         recv_up.copy_(send_down)
         recv_down.copy_(send_up)
+        return
+    if send_up.is_cuda and dist.get_backend(group) == "gloo":
+        # gloo moves host tensors only: stage the faces through host memory
+        host = [t.cpu() for t in (send_up, send_down)] + [torch.empty_like(t, device="cpu") for t in (recv_up, recv_down)]
+        exchange_faces(*host, group=group)
+        recv_up.copy_(host[2])
+        recv_down.copy_(host[3])
         return
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)

@@ -162,3 +162,55 @@ def test_slab_cg_on_one_slab(hr, prec):
     r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
     true = np.linalg.norm(r) / np.linalg.norm(b)
     assert res[0] <= tol and true <= (1.05e-10 if prec == 0 else 2e-4), (it, res, true)
+
+
+def _slab_cg_rank(rank, world, port, q):
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2405_19294_gb300 import hr
+        T, L, N, rep, m0 = 8, 4, 3, "fund", -0.3
+        Tl, V3 = T // world, L ** 3
+        lat = _slabs(hr, T, L, N, rep, world)[rank]      # this rank's slab (all built, one kept)
+        ev = Geometry(T, L).parity == 0
+        b = np.where(ev[:, None, None], inputs.gaussian_spinor(9, T, L, lat.d)[0], 0)
+        fb = _pack(lat, b[None, rank * Tl * V3:(rank + 1) * Tl * V3], 0, 0)
+        fx = lat.new_field(0, 0)
+        it, res = slabs.slab_cg(slabs.SlabDirac(lat, 0), fx, fb, 0, m0, 1e-10)
+        q.put((rank, _unpack(lat, fx, 0, 0), it, res))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_slab_cg_two_processes(hr, world):
+    """slabs.slab_cg over two gloo ranks, each a separate process driving libhr's slab
+    kernels (bulk hop with masked faces, face packing and completion, hr_axpby,
+    hr_norm2) on this GPU; the faces and the FP64 all-reduces go through the host.
+    The kernels of the two processes never wait on each other.  The assembled
+    solution meets the oracle's whole-lattice residual bound."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slab_cg_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    parts = dict((r, (x, it, res)) for r, x, it, res in (q.get(timeout=300) for _ in procs))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert len({parts[r][1] for r in parts}) == 1
+    T, L, N, rep, m0 = 8, 4, 3, "fund", -0.3
+    op = oracle_operator(T, L, N, rep, 1.0, m0, 0.0)
+    x = np.concatenate([parts[r][0] for r in range(world)])
+    ev = op.geom.parity == 0
+    b = np.where(ev[:, None, None], inputs.gaussian_spinor(9, T, L, 3)[0], 0)
+    r = b - op.apply_schur(op.apply_schur(x, 0), 0, dagger=True)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
