@@ -350,7 +350,7 @@ int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int
  * (16 sites per block, link products as MMA tiles); rows = R > 0: the rows kernel for large d_R (R output
  * colour rows per warp, 32 sites per block on the lanes); otherwise
  * split_g = 0: one site per thread with register budget regs = 0 compiler's
- * choice, 1 up to ~170, 2 at most ~85 registers; split_g = G > 0: G threads
+ * choice, 1 up to ~170, 2 at most ~85, 3 at most 128 registers; split_g = G > 0: G threads
  * per site.  -1 if not tuned yet.  The
  * first hr_dphi / hr_cg_solve call for a new shape key times the candidate
  * shapes on the caller's stream (make it outside any stream capture). */

@@ -458,7 +458,8 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 
 // Register budget variants (the autotuner picks one with the block size):
 // MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
-// loads in flight per thread) and 64 x 12 (at most ~85 registers: more warps).
+// loads in flight per thread), 64 x 12 (at most ~85 registers: more warps) and
+// 128 x 4 (at most 128 registers, between the two).
 template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false>
 __global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k, SkipK sk) {
   int64_t tile;
@@ -514,6 +515,7 @@ static void launch_site(const HopK &k, SkipK sk, dim3 grid, int bs, int variant,
   if (k.tmask) hop_kernel<D, REAL, P, 256, 1, true><<<grid, bs, 0, st>>>(k, sk);  // time-slab bulk pass
   else if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k, sk);
   else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k, sk);
+  else if (variant == 3) hop_kernel<D, REAL, P, 128, 4><<<grid, bs, 0, st>>>(k, sk);
   else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k, sk);
 }
 

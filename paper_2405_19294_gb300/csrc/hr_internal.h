@@ -155,7 +155,7 @@ struct HopArgs {
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
 // thread kernel with `bs` threads per block and register-budget variant
 // `regs` (0: compiler's choice for 256 threads, 1: up to ~170 registers,
-// 2: at most ~85 registers); split_g = G > 0 is the colour-split kernel with
+// 2: at most ~85 registers, 3: at most 128 registers); split_g = G > 0 is the colour-split kernel with
 // G threads per site (128 threads per block).
 // mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
 // links staged once per site for all right-hand sides of the block);

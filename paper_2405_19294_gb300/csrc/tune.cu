@@ -40,6 +40,8 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
       out[n++] = HopShape{0, 128, 1, 0};
       out[n++] = HopShape{0, 32, 2, 0};
       out[n++] = HopShape{0, 64, 2, 0};
+      out[n++] = HopShape{0, 32, 3, 0};
+      out[n++] = HopShape{0, 64, 3, 0};
     }
   }
   if (!clover) {
