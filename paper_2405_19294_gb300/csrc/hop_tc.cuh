@@ -16,10 +16,12 @@
 //   kernel does) and FP32 accumulation -- the same roundings as the site
 //   kernel's FP16 x FP16 -> FP32 multiply-adds; the neighbour's site scale is
 //   applied in the reconstruction.
-//   FP32 fields: mma.m16n8k8 on TF32 operands with the three-term split
-//   x = big + small, big = tf32(x), small = tf32(x - big), and
-//   U H ~ U_s H_b + U_b H_s + U_b H_b (small terms first); the dropped U_s H_s
-//   is below 2^-22 of |U||H|, which keeps the FP32 parity bound.
+//   FP32 fields: the same m16n8k16 FP16 tiles on FP16 pairs x = hi + lo
+//   (about 22 significant bits): the half-spinor rows of each (site, rhs,
+//   hop) are first scaled by a power of two into the FP16 range, the link
+//   entries (|U_ij| <= 1) need none, and U H ~ U_lo H_hi + U_hi H_lo + U_hi H_hi
+//   (small terms first; the dropped U_lo H_lo is below 2^-22 of |U||H|) with
+//   FP32 accumulation, which keeps the FP32 parity bound.
 //
 // Fragment layout (PTX mma, row.col, lane = 4 g + t):
 //   A rows 0..7 = Re of output colour 0..7, rows 8..15 = Im;
@@ -56,23 +58,6 @@ constexpr int NW = NT / 32;  // warps per block
 constexpr int RMAX = 12;     // right-hand sides per block (three 4-rhs MMA tiles)
 constexpr int RS = S + 1;    // sum staging: float2 stride between rhs (odd: conflict-free)
 
-__device__ __forceinline__ unsigned f2tf32(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-// x = big + small with both parts TF32
-__device__ __forceinline__ void split_tf32(float x, unsigned &big, unsigned &small) {
-  big = f2tf32(x);
-  small = f2tf32(x - __uint_as_float(big));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 __device__ __forceinline__ void mma_f16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
                                         unsigned b0, unsigned b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -104,10 +89,13 @@ __device__ __forceinline__ float partner_sign(int hh, float sig) { return (MU <=
 // Rows of one site are NCOL = 32 apart plus a pad of 4 words, so the 16 sites
 // written by one warp spread over the banks.  Colours >= D (and the rhs
 // beyond the block's) stay zero from the initial clear.
-constexpr int RW = 12;                 // words per B row
-constexpr int NCOL = 2 * RMAX;         // B rows (fragment columns) per site
-constexpr int SSTR = NCOL * RW + 4;    // words per site
-constexpr int BBUF = S * SSTR;         // words per buffer
+constexpr int NCOL = 2 * RMAX;  // B rows (fragment columns) per site
+template <int P>
+struct Rows {
+  static constexpr int RW = (P == 1) ? 20 : 12;   // words per B row (4 mod 8)
+  static constexpr int SSTR = NCOL * RW + 4;      // words per site
+  static constexpr int BBUF = S * SSTR;           // words per buffer
+};
 
 // The neighbour spinor of one (site, rhs) as loaded for phase 1: 2D float4
 // chunks (FP32) or D uint4 chunks (FP16).  Loading is split from projecting so
@@ -123,22 +111,55 @@ __device__ __forceinline__ void nb_load(Nb<D, P> &nb, const char *f, int64_t Vh,
 #pragma unroll
   for (int c = 0; c < (P == 1 ? 2 * D : D); ++c) nb.v[c] = __ldg(b + (int64_t)c * Vh + j);
 }
+// FP32 fields: the two rows are scaled by a common power of two and stored as
+// FP16 pairs hi + lo (words 0..7 hi, 8..15 lo, each Re pairs then Im pairs);
+// w receives the inverse scale.  FP16 fields: the stored codes (w untouched).
 template <int D, int P, int MU>
-__device__ __forceinline__ void project_store(const Nb<D, P> &nb, float sig, uint32_t *row0, uint32_t *row1) {
+__device__ __forceinline__ void project_store(const Nb<D, P> &nb, float sig, uint32_t *row0, uint32_t *row1,
+                                              float &w) {
   if constexpr (P == 1) {
+    cx<float> h0[D], h1[D];
+    float m = 0.f;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const uint4 a = nb.v[2 * c], b = nb.v[2 * c + 1];
-      cx<float> psi[4], h0, h1;
+      cx<float> psi[4];
       psi[0] = mk(__uint_as_float(a.x), __uint_as_float(a.y));
       psi[1] = mk(__uint_as_float(a.z), __uint_as_float(a.w));
       psi[2] = mk(__uint_as_float(b.x), __uint_as_float(b.y));
       psi[3] = mk(__uint_as_float(b.z), __uint_as_float(b.w));
-      project<MU>(sig, psi, h0, h1);
-      row0[c] = __float_as_uint(h0.x);
-      row0[D + c] = __float_as_uint(h0.y);
-      row1[c] = __float_as_uint(h1.x);
-      row1[D + c] = __float_as_uint(h1.y);
+      project<MU>(sig, psi, h0[c], h1[c]);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(h0[c].x), fabsf(h0[c].y)), fmaxf(fabsf(h1[c].x), fabsf(h1[c].y))));
+    }
+    // power-of-two scale 2^-e with m 2^-e in [0.5, 1): exact, and it brings both
+    // rows into the FP16 range; the sum is multiplied back by 2^e
+    int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 126;
+    e = (m > 0.f) ? max(-100, min(100, e)) : 0;
+    const float sc = __uint_as_float((unsigned)(127 - e) << 23);
+    w = __uint_as_float((unsigned)(127 + e) << 23);
+    // each value -> hi + lo, both FP16: hi = fp16(v), lo = fp16(v - hi)
+    auto split = [&](float a, float b, unsigned &hi, unsigned &lo) {
+      const __half2 h = __floats2half2_rn(a * sc, b * sc);
+      const float2 f = __half22float2(h);
+      hi = h2u(h);
+      lo = h2u(__floats2half2_rn(fmaf(a, sc, -f.x), fmaf(b, sc, -f.y)));
+    };
+    unsigned w0[16], w1[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 2 * q, c1 = (c + 1 < D) ? c + 1 : 0;
+      const bool v0 = c < D, v1 = c + 1 < D;
+      const cx<float> a0 = v0 ? h0[v0 ? c : 0] : mk(0.f, 0.f), b0 = v1 ? h0[c1] : mk(0.f, 0.f);
+      const cx<float> a1 = v0 ? h1[v0 ? c : 0] : mk(0.f, 0.f), b1 = v1 ? h1[c1] : mk(0.f, 0.f);
+      split(a0.x, b0.x, w0[q], w0[8 + q]);      // Re, hi / lo
+      split(a0.y, b0.y, w0[4 + q], w0[12 + q]);  // Im
+      split(a1.x, b1.x, w1[q], w1[8 + q]);
+      split(a1.y, b1.y, w1[4 + q], w1[12 + q]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      reinterpret_cast<uint4 *>(row0)[v] = make_uint4(w0[4 * v], w0[4 * v + 1], w0[4 * v + 2], w0[4 * v + 3]);
+      reinterpret_cast<uint4 *>(row1)[v] = make_uint4(w1[4 * v], w1[4 * v + 1], w1[4 * v + 2], w1[4 * v + 3]);
     }
   } else {
     unsigned h0[D], h1[D];
@@ -163,59 +184,57 @@ __device__ __forceinline__ void project_store(const Nb<D, P> &nb, float sig, uin
   }
 }
 
-// Phase 2, one fragment tile (4 rhs) of one site and hop, FP32 (3xTF32):
-// A from the link matrix (precomputed big / small parts), B from the rows
-// 8k .. 8k+7 of the site, then the rebuild of the four spin rows of
-// (colour g, rhs 4k + t).
-struct AF32 {
-  unsigned xb1, xs1, yb1, ys1, xb2, xs2, yb2, ys2;
+// Phase 2, FP32 fields: the link entries of lane (g, t) -- U(g, 2t), U(g, 2t+1),
+// or conj U(2t, g), conj U(2t+1, g) for the backward hop -- are read from the
+// link slot in global memory one hop ahead (a_fetch) and split into FP16 pairs
+// hi + lo (|U_ij| <= 1, so no scale is needed); rows g (Re out) and g+8 (Im
+// out) against columns 2t, 2t+1 (Re in) and 2t+8, 2t+9 (Im in) as in the FP16
+// tile.
+struct AF32P {
+  unsigned rh, ih, nh, rl, il, nl;  // (Re, Im, -Im) x (hi, lo)
 };
 template <int D, bool ADJ>
-__device__ __forceinline__ AF32 a_f32(const float2 *lrow, int g, int t) {
-  float2 u1 = make_float2(0.f, 0.f), u2 = u1;
+__device__ __forceinline__ void a_fetch(float2 (&u)[2], const float2 *slot, int64_t Vh, int64_t li, int g, int t) {
+  u[0] = u[1] = make_float2(0.f, 0.f);
   if (g < D) {
-    if (t < D) u1 = lrow[ADJ ? t * D + g : g * D + t];
-    if (t + 4 < D) u2 = lrow[ADJ ? (t + 4) * D + g : g * D + t + 4];
+    if (2 * t < D) u[0] = __ldg(slot + (int64_t)(ADJ ? 2 * t * D + g : g * D + 2 * t) * Vh + li);
+    if (2 * t + 1 < D) u[1] = __ldg(slot + (int64_t)(ADJ ? (2 * t + 1) * D + g : g * D + 2 * t + 1) * Vh + li);
   }
+}
+template <bool ADJ>
+__device__ __forceinline__ AF32P a_f32p(float2 u1, float2 u2) {
   if (ADJ) {
     u1.y = -u1.y;
     u2.y = -u2.y;
   }
-  AF32 a;
-  split_tf32(u1.x, a.xb1, a.xs1);
-  split_tf32(u1.y, a.yb1, a.ys1);
-  split_tf32(u2.x, a.xb2, a.xs2);
-  split_tf32(u2.y, a.yb2, a.ys2);
+  AF32P a;
+  const __half2 rh = __floats2half2_rn(u1.x, u2.x), ih = __floats2half2_rn(u1.y, u2.y);
+  const float2 rf = __half22float2(rh), imf = __half22float2(ih);
+  const __half2 rl = __floats2half2_rn(u1.x - rf.x, u2.x - rf.y), il = __floats2half2_rn(u1.y - imf.x, u2.y - imf.y);
+  a.rh = h2u(rh);
+  a.ih = h2u(ih);
+  a.nh = h2u(__hneg2(ih));
+  a.rl = h2u(rl);
+  a.il = h2u(il);
+  a.nl = h2u(__hneg2(il));
   return a;
 }
-template <int D, int MU>
-__device__ __forceinline__ void tile_f32(cx<float> (&acc)[4], const AF32 &a, const uint32_t *rows, float sig, int g,
-                                         int t) {
-  // k-step 0 (Re h columns): A = (Re u1, Im u1, Re u2, Im u2), B = (Re h_t, Re h_t+4);
-  // k-step 1 (Im h columns): A = (-Im u1, Re u1, -Im u2, Re u2), B = (Im h_t, Im h_t+4)
-  const uint32_t *row = rows + g * RW;
-  const float r1 = (t < D) ? __uint_as_float(row[t]) : 0.f;
-  const float r2 = (t + 4 < D) ? __uint_as_float(row[t + 4]) : 0.f;
-  const float i1 = (t < D) ? __uint_as_float(row[D + t]) : 0.f;
-  const float i2 = (t + 4 < D) ? __uint_as_float(row[D + t + 4]) : 0.f;
-  unsigned rb1, rs1, rb2, rs2, ib1, is1, ib2, is2;
-  split_tf32(r1, rb1, rs1);
-  split_tf32(r2, rb2, rs2);
-  split_tf32(i1, ib1, is1);
-  split_tf32(i2, ib2, is2);
-  const unsigned SB = 0x80000000u;  // sign flip (exact on TF32)
+// U H ~ U_lo H_hi + U_hi H_lo + U_hi H_hi (small terms first; the dropped
+// U_lo H_lo is below 2^-22 of |U||H|), FP32 accumulation; w = 2^e undoes the
+// row scale of phase 1
+template <int MU>
+__device__ __forceinline__ void tile_f32p(cx<float> (&acc)[4], const AF32P &a, const uint32_t *rows, float w,
+                                          float sig, int g, int t) {
+  const uint32_t *row = rows + g * Rows<1>::RW;
+  const unsigned bh0 = row[t], bh1 = row[4 + t], bl0 = row[8 + t], bl1 = row[12 + t];
   float c[4] = {0.f, 0.f, 0.f, 0.f};
-  mma_tf32(c, a.xs1, a.ys1, a.xs2, a.ys2, rb1, rb2);
-  mma_tf32(c, a.xb1, a.yb1, a.xb2, a.yb2, rs1, rs2);
-  mma_tf32(c, a.ys1 ^ SB, a.xs1, a.ys2 ^ SB, a.xs2, ib1, ib2);
-  mma_tf32(c, a.yb1 ^ SB, a.xb1, a.yb2 ^ SB, a.xb2, is1, is2);
-  mma_tf32(c, a.xb1, a.yb1, a.xb2, a.yb2, rb1, rb2);
-  mma_tf32(c, a.yb1 ^ SB, a.xb1, a.yb2 ^ SB, a.xb2, ib1, ib2);
-  reconstruct<MU>(sig, mk(c[0], c[2]), mk(c[1], c[3]), acc);
+  mma_f16(c, a.rl, a.il, a.nl, a.rl, bh0, bh1);
+  mma_f16(c, a.rh, a.ih, a.nh, a.rh, bl0, bl1);
+  mma_f16(c, a.rh, a.ih, a.nh, a.rh, bh0, bh1);
+  reconstruct_w<MU>(sig, w, mk(c[0], c[2]), mk(c[1], c[3]), acc);
 }
 
-// The same for FP16 fields (one m16n8k16 tile; w = the neighbour's site scale
-// of the accumulator's rhs)
+// FP16 fields: the link entries as stored (half2), from the staged links
 struct AF16 {
   unsigned ar, ai, an;
 };
@@ -236,24 +255,18 @@ __device__ __forceinline__ AF16 a_f16(const __half2 *lrow, int g, int t) {
   a.an = h2u(__hneg2(ai));
   return a;
 }
-template <int MU>
-__device__ __forceinline__ void tile_f16(cx<float> (&acc)[4], const AF16 &a, const uint32_t *rows, float w, float sig,
-                                         int g, int t) {
-  const uint32_t *row = rows + g * RW;
-  float c[4] = {0.f, 0.f, 0.f, 0.f};
-  mma_f16(c, a.ar, a.ai, a.an, a.ar, row[t], row[4 + t]);
-  reconstruct_w<MU>(sig, w, mk(c[0], c[2]), mk(c[1], c[3]), acc);
-}
 
 // bytes of the dynamic shared memory of one block
 template <int D, int P, bool CLOVER>
 struct Smem {
   static constexpr int NCH = D * D;
-  static constexpr int ES = (P == 1) ? 8 : 4;  // staged link chunk (float2 / half2)
+  static constexpr int ES = 4;                 // staged link chunk (half2; FP16 fields only)
   static constexpr int LST = NCH | 1;          // chunks per staged link row (odd: conflict-free fill)
-  static constexpr size_t LINKS = ((size_t)8 * S * LST * ES + 15) & ~(size_t)15;
-  static constexpr size_t BROWS = (size_t)2 * BBUF * 4;       // two B buffers
-  static constexpr size_t WSC = (size_t)2 * S * RMAX * 4;    // FP16 site scales per buffer
+  // FP16 fields stage the links of the 8 hops; FP32 fields read them per lane
+  // from global memory (their B rows take twice the space)
+  static constexpr size_t LINKS = (P == 2) ? (((size_t)8 * S * LST * ES + 15) & ~(size_t)15) : 0;
+  static constexpr size_t BROWS = (size_t)2 * Rows<P>::BBUF * 4;  // two B buffers
+  static constexpr size_t WSC = (size_t)2 * S * RMAX * 4;    // per-rhs row scales per buffer
   static constexpr size_t CLOV = CLOVER ? (size_t)4 * D * D * S * 8 : 0;
   static constexpr size_t NBI = (size_t)8 * S * sizeof(int64_t);
   // the staged sums (4D x es float2) reuse the link and B-row space after the last hop
@@ -279,6 +292,7 @@ static inline int sum_stride(int R) {
 template <int D, int P, bool CLOVER>
 __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, int es) {
   typedef Smem<D, P, CLOVER> M;
+  constexpr int RW = Rows<P>::RW, SSTR = Rows<P>::SSTR, BBUF = Rows<P>::BBUF;
   extern __shared__ __align__(16) char smem[];
   char *lsm = smem;
   uint32_t *brows = reinterpret_cast<uint32_t *>(smem + M::LINKS);
@@ -318,15 +332,14 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
     nbi[7 * S + s] = ii + (int64_t)(zb - st.z) * LLh;
   }
   for (int w = threadIdx.x; w < 2 * BBUF; w += NT) brows[w] = 0u;  // pads and unused rhs stay zero
-  if (P == 2)
-    for (int w = threadIdx.x; w < 2 * S * RMAX; w += NT) wsc[w] = 0.f;
+  for (int w = threadIdx.x; w < 2 * S * RMAX; w += NT) wsc[w] = 0.f;
   __syncthreads();
   // stage the links of the 8 hops: hop n = 2 mu + back; forward: slot [p][mu] at
   // the output site, backward: slot [1-p][mu] at the backward neighbour
   {
     const int64_t slab = (int64_t)k.nch * Vh;
     const char *lk = reinterpret_cast<const char *>(k.links);
-    for (int e = threadIdx.x; e < 8 * M::NCH * S; e += NT) {
+    for (int e = threadIdx.x; e < (P == 2 ? 8 * M::NCH * S : 0); e += NT) {
       const int ss = e % S, rest = e / S, ch = rest % M::NCH, n = rest / M::NCH;
       if (i0 + ss >= Vh) continue;
       const int mu = n >> 1, back = n & 1;
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
   const char *pin = reinterpret_cast<const char *>(k.in) + (size_t)(rbase + (pq < nr ? pq : 0)) * k.stride;
   const float sg = (float)k.sgn;
   Nb<D, P> nb;
-  float nbw = 0.f;  // FP16: the neighbour's site scale
+  float nbw = 0.f;  // FP16: the neighbour's site scale; FP32: the rows' inverse scale
   auto p1_load = [&](int n) {
     if (!p1) return;
     const int64_t j = nbi[n * S + ps];
@@ -363,12 +376,12 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
     const float sig = (n & 1) ? sg : -sg;
     uint32_t *r0 = brows + buf * BBUF + ps * SSTR + (2 * pq) * RW;
     switch (n >> 1) {
-      case 0: project_store<D, P, 0>(nb, sig, r0, r0 + RW); break;
-      case 1: project_store<D, P, 1>(nb, sig, r0, r0 + RW); break;
-      case 2: project_store<D, P, 2>(nb, sig, r0, r0 + RW); break;
-      default: project_store<D, P, 3>(nb, sig, r0, r0 + RW); break;
+      case 0: project_store<D, P, 0>(nb, sig, r0, r0 + RW, nbw); break;
+      case 1: project_store<D, P, 1>(nb, sig, r0, r0 + RW, nbw); break;
+      case 2: project_store<D, P, 2>(nb, sig, r0, r0 + RW, nbw); break;
+      default: project_store<D, P, 3>(nb, sig, r0, r0 + RW, nbw); break;
     }
-    if (P == 2) wsc[buf * S * RMAX + ps * RMAX + pq] = nbw;
+    wsc[buf * S * RMAX + ps * RMAX + pq] = nbw;
   };
 
   // phase 2: warp w owns sites 2w, 2w+1 of the tile and all NTILE 4-rhs tiles of
@@ -386,12 +399,31 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[a][q][r] = mk(0.f, 0.f);
 
+  // FP32: the link entries of hop n + 1, fetched while hop n computes
+  float2 ua[SPW][2], un[SPW][2];
+  auto a_next = [&](int n) {
+    const int mu = n >> 1, back = n & 1;
+    const float2 *slot = reinterpret_cast<const float2 *>(k.links) + (size_t)(((back ? 1 - p : p) * 4 + mu) * (int64_t)k.nch * Vh);
+#pragma unroll
+    for (int a = 0; a < SPW; ++a) {
+      const int s = SPW * warp + a;
+      const int64_t li = (i0 + s < Vh) ? (back ? nbi[n * S + s] : i0 + s) : 0;
+      if (back) a_fetch<D, true>(un[a], slot, Vh, li, g, t);
+      else a_fetch<D, false>(un[a], slot, Vh, li, g, t);
+    }
+  };
+  if (P == 1) {
+    a_next(0);
+#pragma unroll
+    for (int a = 0; a < SPW; ++a) ua[a][0] = un[a][0], ua[a][1] = un[a][1];
+  }
   p1_load(0);
   p1_store(0, 0);
   cp_async_wait<1>();  // the links are in (the clover may still be streaming)
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     __syncthreads();  // hop n's B rows are written; hop n-1's are no longer read
+    if (P == 1 && n < 7) a_next(n + 1);
     if (n < 7) {  // FP16: the loads stay in flight during the MMA tiles of hop n
       p1_load(n + 1);
       if (P == 1) p1_store(n + 1, (n + 1) & 1);  // FP32: too many registers to hold them
@@ -403,11 +435,12 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
       const int s = SPW * warp + a;
       const char *lrow = lsm + (size_t)(n * S + s) * M::LST * M::ES;
       const uint32_t *rows = bb + s * SSTR;
+      const float *wr = wsc + (n & 1) * S * RMAX + s * RMAX + t;
 #define HR_TC_SITE(MU, ADJ)                                                                               \
   if (P == 1) {                                                                                           \
-    const AF32 af = a_f32<D, ADJ>(reinterpret_cast<const float2 *>(lrow), g, t);                          \
+    const AF32P af = a_f32p<ADJ>(ua[a][0], ua[a][1]);                                                     \
     _Pragma("unroll") for (int q = 0; q < NTILE; ++q)                                                     \
-      tile_f32<D, MU>(acc[a][q], af, rows + q * 8 * RW, sig, g, t);                                       \
+      tile_f32p<MU>(acc[a][q], af, rows + q * 8 * RW, wr[4 * q], sig, g, t);                              \
   } else {                                                                                                \
     const AF16 af = a_f16<D, ADJ>(reinterpret_cast<const __half2 *>(lrow), g, t);                         \
     float c[NTILE][4];                                                                                    \
@@ -416,9 +449,8 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
       c[q][0] = c[q][1] = c[q][2] = c[q][3] = 0.f;                                                        \
       mma_f16(c[q], af.ar, af.ai, af.an, af.ar, row[t], row[4 + t]);                                      \
     }                                                                                                     \
-    const float *w = wsc + (n & 1) * S * RMAX + s * RMAX + t;                                             \
     _Pragma("unroll") for (int q = 0; q < NTILE; ++q)                                                     \
-      reconstruct_w<MU>(sig, w[4 * q], mk(c[q][0], c[q][2]), mk(c[q][1], c[q][3]), acc[a][q]);            \
+      reconstruct_w<MU>(sig, wr[4 * q], mk(c[q][0], c[q][2]), mk(c[q][1], c[q][3]), acc[a][q]);           \
   }
       switch (n) {
         case 0: HR_TC_SITE(0, false) break;
@@ -433,6 +465,9 @@ __global__ void __launch_bounds__(NT, 2) hop_tc_kernel(HopK k, SkipK sk, int R, 
 #undef HR_TC_SITE
     }
     if (n < 7 && P == 2) p1_store(n + 1, (n + 1) & 1);
+    if (P == 1 && n < 7)
+#pragma unroll
+      for (int a = 0; a < SPW; ++a) ua[a][0] = un[a][0], ua[a][1] = un[a][1];
   }
   __syncthreads();  // the link and B-row space becomes the sum staging
   if (g < D) {
