@@ -31,18 +31,20 @@
 //   so each lane rebuilds the four spin rows of (colour g, rhs t) from its
 //   own accumulator registers.
 //
-// Work split.  A block covers S = 16 consecutive output sites x R <= 16 rhs.
-//   0. The links of all 8 hops of the S sites (row-major per site, so a warp
-//      reads one site's matrix from one shared-memory row) and, with clover,
-//      the packed A or A^{-1} blocks are staged by cp.async.
+// Work split.  A block covers S = 16 consecutive output sites x R <= 12 rhs.
+//   0. With clover, the packed A or A^{-1} blocks are staged by cp.async; for
+//      FP16 fields so are the links of all 8 hops of the S sites (row-major per
+//      site, so a warp reads one site's matrix from one shared-memory row).
+//      FP32 fields, whose B rows take twice the space, read each lane's two
+//      link entries from global memory one hop ahead.
 //   Then, hop by hop (double-buffered, one barrier per hop):
 //   1. one thread per (site, rhs) loads the neighbour spinor of the next hop
 //      (coalesced: consecutive threads read consecutive sites), projects it
 //      and writes the two half-spinor rows to shared memory in B-fragment
 //      order;
-//   2. each warp runs the MMA tiles of its (site, 4-rhs tile) units of the
-//      current hop from shared memory and rebuilds the spin rows into its
-//      accumulator registers.
+//   2. each warp runs the MMA tiles of its two sites (three 4-rhs tiles each)
+//      for the current hop from shared memory and rebuilds the spin rows into
+//      its accumulator registers.
 //   3. After the last hop the sums go through shared memory to one thread per
 //      (site, rhs), which runs the epilogue of the multi-rhs kernel (scaling,
 //      clover, self term, store).

@@ -160,7 +160,7 @@ struct HopArgs {
 // mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
 // links staged once per site for all right-hand sides of the block);
 // mrhs = HR_TC_MRHS + 16 the tensor-core multi-right-hand-side kernel
-// (hop_tc.cuh: 16 sites per block, the link products of up to 16 rhs as MMA
+// (hop_tc.cuh: 16 sites per block, the link products of up to 12 rhs as MMA
 // tiles; FP32 and FP16, complex d_R = 3 ... 6).
 // rows = R > 0 selects the rows kernel: R output colour rows per warp,
 // ceil(d/R) warps per block, 32 sites per block on the lanes.
@@ -229,7 +229,7 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
-// tensor-core multi-rhs kernel (complex d_R = 3 ... 6), FP32 (3xTF32) / FP16
+// tensor-core multi-rhs kernel (complex d_R = 3 ... 6), FP32 (FP16 pairs) / FP16
 int hr_launch_hop_tc_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
 int hr_launch_hop_tc_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
 static inline bool hr_has_tc_mrhs(int d, int is_real, int prec) {
