@@ -235,7 +235,9 @@ int hr_unpack_spinor(hr_lattice *lat, double *canonical, const void *internal, i
  * With FP16 fields the projected half-spinor may be rounded to FP16 before
  * the link product (FP16 x FP16 -> FP32 multiply-add); the relative error
  * against FP64 stays about 3e-4 of the field norm.  csw must equal the value given to hr_represent_links.  `in` and `out`
- * must not overlap.  Two hopping launches, no host synchronisation. */
+ * must not overlap.  Two hopping launches (the second, for the one-site-per-thread
+ * kernel, a programmatic dependent launch that starts while the first one
+ * finishes), no host synchronisation. */
 int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw,
             int prec, int nrhs, int dagger);
 

@@ -485,6 +485,7 @@ int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, do
   a.coef = 0.5;
   a.diag = diag;
   a.clover = clover ? clover_ptr(lat, prec, false, p) : nullptr;
+  a.pdl = 1;  // the site kernel may launch while the first hop finishes (it waits for its results)
   HR_TRY(hr_launch_hop(lat, prec, a, st));
   lat->hop_launches += 2;
   return HR_OK;

@@ -460,8 +460,18 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 // MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
 // loads in flight per thread), 64 x 12 (at most ~85 registers: more warps) and
 // 128 x 4 (at most 128 registers, between the two).
+// Programmatic dependent launch: every block lets the next kernel of the
+// stream start launching, and waits for the previous kernel's results (it
+// reads the fields that kernel wrote) before anything else; both are no-ops
+// unless the kernels were launched with programmatic stream serialisation.
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false>
 __global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k, SkipK sk) {
+  pdl_start();
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
@@ -510,13 +520,34 @@ static inline HopK make_hopk(const hr_lattice *lat, const HopArgs &a) {
   return k;
 }
 
+// launch one site-kernel instance; pdl: programmatic stream serialisation (the
+// kernel may start while the previous one on the stream finishes)
+template <typename Kern>
+static void launch_pdl(Kern kern, const HopK &k, SkipK sk, dim3 grid, int bs, cudaStream_t st, int pdl) {
+  if (!pdl) {
+    kern<<<grid, bs, 0, st>>>(k, sk);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, k, sk);
+}
+
 template <int D, bool REAL, int P>
-static void launch_site(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st) {
-  if (k.tmask) hop_kernel<D, REAL, P, 256, 1, true><<<grid, bs, 0, st>>>(k, sk);  // time-slab bulk pass
-  else if (variant == 1) hop_kernel<D, REAL, P, 128, 3><<<grid, bs, 0, st>>>(k, sk);
-  else if (variant == 2) hop_kernel<D, REAL, P, 64, 12><<<grid, bs, 0, st>>>(k, sk);
-  else if (variant == 3) hop_kernel<D, REAL, P, 128, 4><<<grid, bs, 0, st>>>(k, sk);
-  else hop_kernel<D, REAL, P, 256, 1><<<grid, bs, 0, st>>>(k, sk);
+static void launch_site(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {
+  if (k.tmask) launch_pdl(hop_kernel<D, REAL, P, 256, 1, true>, k, sk, grid, bs, st, pdl);  // time-slab bulk pass
+  else if (variant == 1) launch_pdl(hop_kernel<D, REAL, P, 128, 3>, k, sk, grid, bs, st, pdl);
+  else if (variant == 2) launch_pdl(hop_kernel<D, REAL, P, 64, 12>, k, sk, grid, bs, st, pdl);
+  else if (variant == 3) launch_pdl(hop_kernel<D, REAL, P, 128, 4>, k, sk, grid, bs, st, pdl);
+  else launch_pdl(hop_kernel<D, REAL, P, 256, 1>, k, sk, grid, bs, st, pdl);
 }
 
 // Launch the site-per-thread kernel for (D, REAL) of precision P with `bs`
@@ -529,19 +560,19 @@ int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int b
   const int d = lat->d;
   if (lat->is_real) {
     switch (d) {
-      case 3: launch_site<3, true, P>(k, sk, grid, bs, variant, st); break;
-      case 8: launch_site<8, true, P>(k, sk, grid, bs, variant, st); break;
+      case 3: launch_site<3, true, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 8: launch_site<8, true, P>(k, sk, grid, bs, variant, st, a.pdl); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   } else {
     switch (d) {
-      case 2: launch_site<2, false, P>(k, sk, grid, bs, variant, st); break;
-      case 3: launch_site<3, false, P>(k, sk, grid, bs, variant, st); break;
-      case 4: launch_site<4, false, P>(k, sk, grid, bs, variant, st); break;
-      case 5: launch_site<5, false, P>(k, sk, grid, bs, variant, st); break;
-      case 6: launch_site<6, false, P>(k, sk, grid, bs, variant, st); break;
-      case 7: launch_site<7, false, P>(k, sk, grid, bs, variant, st); break;
-      case 8: launch_site<8, false, P>(k, sk, grid, bs, variant, st); break;
+      case 2: launch_site<2, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 3: launch_site<3, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 4: launch_site<4, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 5: launch_site<5, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 6: launch_site<6, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 7: launch_site<7, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
+      case 8: launch_site<8, false, P>(k, sk, grid, bs, variant, st, a.pdl); break;
       default: return HR_ERR_UNSUPPORTED;
     }
   }

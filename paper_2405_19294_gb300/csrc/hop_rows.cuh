@@ -416,12 +416,23 @@ static int rows_smem_optin(F *fn, size_t bytes) {
   HR_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return HR_OK;
 }
+// the opt-in once per device and kernel (the attribute is per device)
+template <typename F>
+static int rows_smem_optin_once(F *fn, size_t bytes, unsigned long long &done) {
+  int dev = 0;
+  HR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev > 63) return HR_ERR_UNSUPPORTED;
+  if ((done >> dev) & 1ull) return HR_OK;
+  HR_TRY(rows_smem_optin(fn, bytes));
+  done |= 1ull << dev;
+  return HR_OK;
+}
 
 template <int D, bool REAL, int P, int R>
 int launch_rows(const HopK &k, SkipK sk, int nrhs, cudaStream_t st) {
   constexpr size_t sm = rows_smem_bytes<D, REAL, R, P>();
-  static int opt = rows_smem_optin(hop_rows_kernel<D, REAL, P, R>, sm);
-  if (opt != HR_OK) return opt;
+  static unsigned long long done = 0;
+  HR_TRY(rows_smem_optin_once(hop_rows_kernel<D, REAL, P, R>, sm, done));
   dim3 grid((unsigned)(((k.Vh + 31) / 32) * nrhs));
   hop_rows_kernel<D, REAL, P, R><<<grid, RowsGeom<D, REAL, R>::NT, sm, st>>>(k, sk);
   return hr_check_launch("hop_rows_kernel");
@@ -449,7 +460,8 @@ static const void *rows_multi_ptr(int d, int is_real, int rows, int *block, size
   if (d == DD && real == RE && rows == RR) {                                      \
     *block = RowsGeom<DD, RE, RR>::NT;                                            \
     *smem = rows_smem_bytes<DD, RE, RR, P>();                                     \
-    static int opt = rows_smem_optin(hop_rows_multi_kernel<DD, RE, P, RR>, *smem); \
+    static unsigned long long done = 0;                                             \
+    const int opt = rows_smem_optin_once(hop_rows_multi_kernel<DD, RE, P, RR>, *smem, done); \
     return opt == HR_OK ? (const void *)hop_rows_multi_kernel<DD, RE, P, RR> : nullptr; \
   }
   HR_ROWS_SHAPES(HR_ROWS_CASE)

@@ -512,15 +512,18 @@ int launch(const HopK &k, SkipK sk, cudaStream_t st) {
   const int64_t tiles = (k.Vh + S - 1) / S;
   const int es = sum_stride(R);
   const size_t smem = Smem<D, P, CLOVER>::bytes(es);
-  static bool attr = false;  // the largest block size is set once (R <= RMAX)
-  if (!attr) {
+  // the largest block size (R = RMAX) is opted in once per device
+  static unsigned long long attr = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev > 63) return HR_ERR_CUDA;
+  if (!((attr >> dev) & 1ull)) {
     const cudaError_t e = cudaFuncSetAttribute(hop_tc_kernel<D, P, CLOVER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)Smem<D, P, CLOVER>::bytes(sum_stride(RMAX)));
     if (e != cudaSuccess) {
       hr_note_cuda_error(e, "cudaFuncSetAttribute(hop_tc_kernel)", __FILE__, __LINE__);
       return HR_ERR_CUDA;
     }
-    attr = true;
+    attr |= 1ull << dev;
   }
   hop_tc_kernel<D, P, CLOVER><<<(unsigned)(tiles * nrb), NT, smem, st>>>(k, sk, R, es);
   return hr_check_launch("hop_tc_kernel");

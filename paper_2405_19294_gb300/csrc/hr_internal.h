@@ -150,6 +150,7 @@ struct HopArgs {
   int tmask;              // 1: skip the t hops that cross the slab faces (sub-domain bulk pass)
   const double *skip_rr;  // with skip_stop: a rhs whose skip_rr <= skip_stop is done, its blocks
   const double *skip_stop;  // return at once (CG chunks past convergence); null = never skip
+  int pdl;                  // 1: programmatic dependent launch after the previous hop (site kernel)
 };
 
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-

@@ -6,8 +6,8 @@
 // colour-split kernel with G threads per site.  The first launch with a new
 // key (precision, d_R, real, clover, multi-rhs, slab, log2 of the volume)
 // times every candidate shape with CUDA events on the caller's stream (two
-// sweeps of one warm-up and four timed launches each, keeping each shape's
-// faster sweep, on the caller's own buffers -- the kernel is a pure function
+// sweeps of one warm-up and 4 (16 on small lattices) timed launches each,
+// keeping each shape's faster sweep, on the caller's own buffers -- the kernel is a pure function
 // of its inputs, so repeating it is harmless) and keeps the fastest.  While the stream is being captured into a CUDA graph no timing is
 // possible; the cached choice, else the first candidate, is used.  Setting
 // HR_TUNE=0 in the environment disables tuning (first candidate always).
@@ -116,15 +116,18 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
   cudaEvent_t e0 = e0_owner.e, e1 = e1_owner.e;
   // two sweeps over the candidates (the second in reverse order, so that no
   // shape always runs right after the same neighbour); each candidate keeps
-  // the faster of its two timings of 4 launches
+  // the faster of its two timings of `reps` launches: 4 on large lattices,
+  // 16 below 2^20 sites per parity, where one launch lasts only tens of
+  // microseconds and 4 of them did not separate shapes 8 % apart
   float t[HR_MAX_SHAPES];
   for (int c = 0; c < n; ++c) t[c] = 1e30f;
+  const int reps = lat->Vh < ((int64_t)1 << 20) ? 16 : 4;
   for (int sweep = 0; sweep < 2; ++sweep)
     for (int cc = 0; cc < n; ++cc) {
       const int c = sweep ? n - 1 - cc : cc;
       if (launch_shape(lat, prec, a, s, shapes[c]) != HR_OK) continue;  // warm-up; unsupported shapes drop out
       HR_CUDA(cudaEventRecord(e0, s));
-      for (int r = 0; r < 4; ++r) HR_TRY(launch_shape(lat, prec, a, s, shapes[c]));
+      for (int r = 0; r < reps; ++r) HR_TRY(launch_shape(lat, prec, a, s, shapes[c]));
       HR_CUDA(cudaEventRecord(e1, s));
       HR_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
