@@ -277,15 +277,17 @@ def _pack_rhs(lat, inputs, torch, seed, T, L, nrhs, prec, parity=0):
     return f
 
 
-def _timed_cg(lat, fx, fb, m0, csw, inner, nrhs=1, inner_tol=0.0, reps=2):
+def _timed_cg(lat, fx, fb, m0, csw, inner, nrhs=1, inner_tol=0.0, reps=2, outer=3):
+    """Wall time of a CG solve to 1e-10 (mixed: outer residuals in float-float, outer=3, or FP64, 0)."""
     import torch
     res = None
     for _ in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = lat.cg_solve(fx, fb, 0, m0, csw, 1e-10, inner_prec=inner, inner_tol=inner_tol, nrhs=nrhs,
-                           check_every=20, raise_on_error=False)
+                           check_every=20, raise_on_error=False, outer_prec=outer)
         res["wall_s"] = round(time.perf_counter() - t0, 4)
+    res["outer"] = None if inner == 0 else ("ff" if outer == 3 else "fp64")
     return res
 
 
@@ -436,7 +438,7 @@ def run_one_dhat(spec):
     csw = float(parts[6]) if len(parts) > 6 else 0.0
     nrhs = int(parts[7]) if len(parts) > 7 else 1
     N, T, L = int(N), int(T), int(L)
-    prec = {"f64": hr.F64, "f32": hr.F32, "f16": hr.F16}[prec]
+    prec = hr.PREC[prec]
     lat = _lattice(hr, inputs, torch, T, L, N, rep, 1.0, csw)
     fi = _pack_rhs(lat, inputs, torch, 1, T, L, nrhs, prec)
     fo = lat.new_field(0, prec, nrhs)
@@ -525,14 +527,19 @@ def _suite_bicgstab(hr, inputs, torch):
     fx = lat.new_field(0, hr.F64)
     line = {"suite": "SU(3) fund 32^3x64: BiCGstab on Dhat vs CG on Dhat^+Dhat, to 1e-10", "m0": m0,
             "note": "BiCGstab residual is |b - Dhat x|/|b|; CG residual is that of the normal system"}
-    for name, fn, inner in (("cg_fp64", lat.cg_solve, hr.F64), ("cg_mixed_fp32", lat.cg_solve, hr.F32),
-                            ("bicgstab_fp64", lat.bicgstab_solve, hr.F64),
-                            ("bicgstab_mixed_fp32", lat.bicgstab_solve, hr.F32)):
+    # mixed solves: outer residuals in float-float, and in FP64 (_fp64_outer)
+    for name, fn, inner, outer in (("cg_fp64", lat.cg_solve, hr.F64, hr.F64),
+                                   ("cg_mixed_fp32", lat.cg_solve, hr.F32, hr.FF),
+                                   ("cg_mixed_fp32_fp64_outer", lat.cg_solve, hr.F32, hr.F64),
+                                   ("bicgstab_fp64", lat.bicgstab_solve, hr.F64, hr.F64),
+                                   ("bicgstab_mixed_fp32", lat.bicgstab_solve, hr.F32, hr.FF),
+                                   ("bicgstab_mixed_fp32_fp64_outer", lat.bicgstab_solve, hr.F32, hr.F64)):
         r = None
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = fn(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=inner, check_every=10, raise_on_error=False)
+            r = fn(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=inner, check_every=10, raise_on_error=False,
+                   outer_prec=outer)
             r["wall_s"] = round(time.perf_counter() - t0, 4)
         line[name] = {k: r[k] for k in ("wall_s", "iterations", "outer_steps", "true_residual", "status")}
     print(json.dumps(line), flush=True)
@@ -652,8 +659,11 @@ def _ev_ms(torch, fn, reps, flush=None):
 
 
 def _cg_rec(res):
-    return {"seconds": round(res["wall_s"], 4), "iterations": res["iterations"], "outer_steps": res["outer_steps"],
-            "true_residual": res["true_residual"], "status": res["status"]}
+    rec = {"seconds": round(res["wall_s"], 4), "iterations": res["iterations"], "outer_steps": res["outer_steps"],
+           "true_residual": res["true_residual"], "status": res["status"]}
+    if res.get("outer"):
+        rec["outer_residuals"] = res["outer"]
+    return rec
 
 
 def _rel_diff(torch, lat, f_lo, prec, f64, nrhs=1):
@@ -738,7 +748,7 @@ def config3(hr, inputs, torch, flush, peak, nr=12):
             rec["dhat_12x1rhs_fp32_ms"] = round(ms1, 3)
         del fi, fo
     del o64
-    for prec, k in ((hr.F32, nr), (hr.F16, nr), (hr.F64, 1)):
+    for prec, k in ((hr.F32, nr), (hr.F16, nr), (hr.F64, 1), (hr.FF, nr), (hr.F64, nr)):
         _warm(lat, prec, k, m0, csw)
     fx = lat.new_field(0, hr.F64, nr)
     cg = {}
@@ -746,6 +756,8 @@ def config3(hr, inputs, torch, flush, peak, nr=12):
     cg["mixed_fp32_12rhs"] = dict(_cg_rec(r32), seconds_per_rhs=round(r32["wall_s"] / nr, 4))
     r16 = _timed_cg(lat, fx, fb, m0, csw, hr.F16, nrhs=nr, inner_tol=3e-3, reps=1)
     cg["mixed_fp16_12rhs"] = dict(_cg_rec(r16), seconds_per_rhs=round(r16["wall_s"] / nr, 4), inner_tol=3e-3)
+    r32d = _timed_cg(lat, fx, fb, m0, csw, hr.F32, nrhs=nr, reps=1, outer=hr.F64)
+    cg["mixed_fp32_12rhs_fp64_outer"] = dict(_cg_rec(r32d), seconds_per_rhs=round(r32d["wall_s"] / nr, 4))
     fb1 = lat.new_field(0, hr.F64)
     fx1 = lat.new_field(0, hr.F64)
     fb1.copy_(fb[:lat.field_bytes(0, hr.F64, 1)])
@@ -869,9 +881,9 @@ def main():
     if args.shape:
         regs, g, bs = (int(v) for v in args.shape.split(","))
         lat.set_shape(TP, (g, bs, regs))
-    fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16)}
-    fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16)}
-    for p in (hr.F64, hr.F32, hr.F16):
+    fin = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16, hr.FF)}
+    fout = {p: lat.new_field(hr.EVEN, p) for p in (hr.F64, hr.F32, hr.F16, hr.FF)}
+    for p in (hr.F64, hr.F32, hr.F16, hr.FF):
         lat.pack(fin[p], src, hr.EVEN, p)
     flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")   # 512 MiB, read to evict L2
     m0, csw = wl["m0"], wl["csw"]
@@ -911,6 +923,10 @@ def main():
     for _ in range(3):
         lat.dphi(fout[hr.F64], fin[hr.F64], hr.EVEN, m0, csw, hr.F64)
     ms64 = float(np.mean(timed(hr.F64, max(3, args.steps // 4))))
+    # the same FP64-accurate Dhat in float-float arithmetic (the mixed solvers' outer residuals)
+    for _ in range(3):
+        lat.dphi(fout[hr.FF], fin[hr.FF], hr.EVEN, m0, csw, hr.FF)
+    msff = float(np.mean(timed(hr.FF, max(3, args.steps // 4))))
     # FP16 Dhat (per-site scaled FP16 storage, FP32 arithmetic), unless it is the timed precision
     peaks, kind = measured_peaks()
     fp16 = None
@@ -993,19 +1009,24 @@ def main():
         fb = lat.new_field(hr.EVEN, hr.F64)
         fx = lat.new_field(hr.EVEN, hr.F64)
         lat.pack(fb, src, hr.EVEN, hr.F64)
-        for name, inner in (("fp64", hr.F64), ("mixed_fp32", hr.F32), ("mixed_fp16", hr.F16)):
+        # mixed solves: outer residuals in float-float (the default) and in FP64
+        for name, inner, outer in (("fp64", hr.F64, hr.F64), ("mixed_fp32", hr.F32, hr.FF),
+                                   ("mixed_fp16", hr.F16, hr.FF), ("mixed_fp32_fp64_outer", hr.F32, hr.F64),
+                                   ("mixed_fp16_fp64_outer", hr.F16, hr.F64)):
             res = None
             for rep_ in range(2):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 res = lat.cg_solve(fx, fb, hr.EVEN, m0, csw, 1e-10, inner_prec=inner, check_every=20,
-                                   raise_on_error=False)
+                                   raise_on_error=False, outer_prec=outer)
                 res["wall_s"] = time.perf_counter() - t0
             cg[name] = {"seconds": round(res["wall_s"], 4), "iterations": res["iterations"],
                         "outer_steps": res["outer_steps"], "true_residual": res["true_residual"],
                         "status": res["status"]}
+            if inner != hr.F64:
+                cg[name]["outer_residuals"] = "ff" if outer == hr.FF else "fp64"
         if cg["fp64"]["seconds"] > 0:
-            for k in ("mixed_fp32", "mixed_fp16"):
+            for k in ("mixed_fp32", "mixed_fp16", "mixed_fp32_fp64_outer", "mixed_fp16_fp64_outer"):
                 cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[k]["seconds"], 2)
 
     # the other workloads (configs 2, 3, 4), inside the same clock record
@@ -1036,6 +1057,11 @@ def main():
                             "overlap step k's kernels (copy streams, double-buffered staging)"},
             "fp64": {"ms_per_step": round(ms64, 4), "gbs": round(b64 / (ms64 * 1e-3) / 1e9, 2),
                      "tflops": round(fl / (ms64 * 1e-3) / 1e12, 3), "bound": "alu (FP64)"},
+            "ff": {"ms_per_step": round(msff, 4), "gbs": round(b64 / (msff * 1e-3) / 1e9, 2),
+                   "frac_of_measured_hbm": round(b64 / (msff * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                   "speedup_vs_fp64": round(ms64 / msff, 2), "shape": lat.tuned_shape(hr.FF),
+                   "rel_err_vs_fp64": _rel_diff(torch, lat, fout[hr.FF], hr.FF, fout[hr.F64]),
+                   "arithmetic": "float-float (FP32 pairs, 48 bits), FP64 bytes"},
             "fp16": fp16, "cg": cg, "configs": configs, "clocks": clk, "wall_timed_s": round(wall, 3)}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_leg()

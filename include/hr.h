@@ -60,7 +60,15 @@ typedef struct hr_lattice hr_lattice;
 typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
 /* EVEN/ODD: the Schur complement Dhat on that parity; FULL: D on the whole lattice */
 typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2 } hr_parity;
-typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2 } hr_prec;
+/* HR_FF: float-float, each real the unevaluated sum hi + lo of two FP32
+ * numbers (about 48 significant bits, FP32 exponent range), stored in the FP64
+ * layout with each 16-byte chunk (re.hi, re.lo, im.hi, im.lo); the FP64-accurate
+ * operator of the mixed solvers' outer residuals, for a part whose FP64 units
+ * run at a small fraction of its FP32 rate.  Accepted by hr_field_bytes,
+ * hr_pack_spinor / hr_unpack_spinor, hr_dphi (d_R <= 8 classes of the
+ * one-site-per-thread kernel, whole lattices), the shape calls, and
+ * hr_cg_params.outer_prec. */
+typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2, HR_FF = 3 } hr_prec;
 
 typedef enum {
   HR_OK = 0,
@@ -91,12 +99,15 @@ typedef struct {
   double inner_tol;  /* relative residual reduction per inner solve (mixed only) */
   int nrhs;          /* number of right-hand sides stored back to back */
   int check_every;   /* inner iterations between residual checks on the host */
+  int outer_prec;    /* mixed hr_cg_solve / hr_bicgstab_solve: arithmetic of the outer
+                        residual, HR_F64 (0) or HR_FF (float-float; where the class
+                        has no float-float kernel FP64 is used).  Ignored elsewhere */
 } hr_cg_params;
 
 typedef struct {
   int iterations;      /* inner CG iterations, summed over outer steps (max over rhs) */
   int outer_steps;     /* FP64 residual recomputations (1 for plain FP64 CG) */
-  double true_residual;/* max over rhs of |b - M x| / |b| in FP64 at exit */
+  double true_residual;/* max over rhs of |b - M x| / |b| at exit (outer arithmetic) */
   double seconds;      /* wall time of the call */
   double hop_launches; /* hopping-kernel launches issued */
 } hr_cg_stats;
@@ -290,7 +301,9 @@ int hr_norm2_static(const void *x, int64_t half_volume, int d, int parity, int p
  * for nrhs FP64 internal fields, to a true FP64 relative residual
  * params->tol per rhs.  inner_prec = HR_F64: plain CG.  HR_F32 / HR_F16:
  * the inner CG runs in that precision (FP32 accumulation) and an FP64
- * defect-correction loop recomputes b - M x in FP64 until params->tol.
+ * defect-correction loop recomputes b - M x in FP64 until params->tol
+ * (params->outer_prec = HR_FF: in float-float, the iterate kept as a
+ * float-float field and rounded to FP64 into x at exit).
  * x is overwritten (initial guess ignored: x0 = 0).  Synchronous.
  * Errors: HR_ERR_NOT_CONVERGED (stats still filled), HR_ERR_BREAKDOWN. */
 int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, double m0, double csw,
@@ -371,8 +384,9 @@ int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, in
  * BiCGstab (Sec. 3.3; van der Vorst's stabilised bi-conjugate gradient), for
  * nrhs FP64 internal fields, to a true FP64 relative residual
  * |b - A x| / |b| <= params->tol per rhs.  inner_prec HR_F64: plain FP64
- * BiCGstab; HR_F32: FP32 inner BiCGstab inside FP64 defect correction.
- * x overwritten (x0 = 0).  Synchronous.  The solver's workspace is shared
+ * BiCGstab; HR_F32: FP32 inner BiCGstab inside FP64 defect correction
+ * (params->outer_prec = HR_FF: outer residuals in float-float, as for
+ * hr_cg_solve).  x overwritten (x0 = 0).  Synchronous.  The solver's workspace is shared
  * by all lattices of the process: do not call it concurrently from several
  * threads.  Errors: HR_ERR_ARG (HR_F16 inner not offered),
  * HR_ERR_NOT_CONVERGED, HR_ERR_BREAKDOWN (rho or <t,t> vanished). */

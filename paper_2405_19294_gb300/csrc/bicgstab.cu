@@ -541,11 +541,25 @@ extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int pa
     mone[k] = -1.0;
   }
   const size_t bytes64 = fb64 * nsub * nrhs;
+  // outer residuals in float-float where that operator is built (mixed solves):
+  // the iterate and b then live in the FP64 workspace's x and r buffers, which
+  // the mixed solve does not otherwise use
+  HopShape ffs[HR_MAX_SHAPES];
+  const int po = (lo != HR_F64 && prm->outer_prec == HR_FF && !lat->dom &&
+                  hr_hop_shapes(lat->d, lat->is_real, HR_FF, csw != 0.0, nrhs > 1, ffs) > 0)
+                     ? HR_FF
+                     : HR_F64;
+  void *xo = po == HR_FF ? g_bi->f[HR_F64][0] : x;
+  const void *bo = po == HR_FF ? g_bi->f[HR_F64][1] : b;
   HR_CUDA(cudaMemsetAsync(x, 0, bytes64, s));
   HR_TRY(setv(sa, one));
   HR_TRY(setv(sb, zero));
-  HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, R, f64, f64, nrhs, sa, sb, red, 1, s));
+  HR_TRY(hr_blas_axpby(HR_F64, po, b, R, f64, f64, nrhs, sa, sb, red, 1, s));
   HR_TRY(norms(bn2));
+  if (po == HR_FF) {
+    HR_CUDA(cudaMemcpyAsync(g_bi->f[HR_F64][1], R, bytes64, cudaMemcpyDeviceToDevice, s));
+    HR_CUDA(cudaMemsetAsync(xo, 0, bytes64, s));
+  }
   for (int r = 0; r < nrhs; ++r) rn2[r] = bn2[r];
   const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : 1e-5;
   const int check_every = prm->check_every > 0 ? prm->check_every : 10;
@@ -572,26 +586,31 @@ extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int pa
     HR_TRY(setv(sa, a));
     HR_TRY(setv(sb, zero));
     char **F = reinterpret_cast<char **>(g_bi->f[lo]);
-    HR_TRY(hr_blas_axpby(HR_F64, lo, R, F[1], f64, flo, nrhs, sa, sb, red, 0, s));
+    HR_TRY(hr_blas_axpby(po, lo, R, F[1], f64, flo, nrhs, sa, sb, red, 0, s));
     HR_CUDA(cudaMemsetAsync(F[0], 0, fblo * nsub * nrhs, s));
     int done = 0;
     status = bi_loop(c, stop, check_every, maxit - iters, &done);
     iters += done;
     ++outer;
     if (status != HR_OK) break;
-    // x += |R| e (FP64); R = b - A x
+    // x += |R| e; R = b - A x (in precision po)
     for (int r = 0; r < nrhs; ++r) a[r] = sqrt(rn2[r]);
     HR_TRY(setv(sa, a));
     HR_TRY(setv(sb, one));
-    HR_TRY(hr_blas_axpby(lo, HR_F64, F[0], x, flo, f64, nrhs, sa, sb, red, 0, s));
-    HR_TRY(hr_dphi_impl(lat, AX, x, parity, m0, csw, HR_F64, nrhs, 0, s));
+    HR_TRY(hr_blas_axpby(lo, po, F[0], xo, flo, f64, nrhs, sa, sb, red, 0, s));
+    HR_TRY(hr_dphi_impl(lat, AX, xo, parity, m0, csw, po, nrhs, 0, s));
     HR_TRY(setv(sa, one));
     HR_TRY(setv(sb, zero));
-    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, R, f64, f64, nrhs, sa, sb, red, 0, s));
+    HR_TRY(hr_blas_axpby(po, po, bo, R, f64, f64, nrhs, sa, sb, red, 0, s));
     HR_TRY(setv(sa, mone));
     HR_TRY(setv(sb, one));
-    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, AX, R, f64, f64, nrhs, sa, sb, red, 1, s));
+    HR_TRY(hr_blas_axpby(po, po, AX, R, f64, f64, nrhs, sa, sb, red, 1, s));
     HR_TRY(norms(rn2));
+  }
+  if (po == HR_FF) {  // x = the FP64 value of the float-float iterate
+    HR_TRY(setv(sa, one));
+    HR_TRY(setv(sb, zero));
+    HR_TRY(hr_blas_axpby(HR_FF, HR_F64, xo, x, f64, f64, nrhs, sa, sb, red, 0, s));
   }
   HR_CUDA(cudaStreamSynchronize(s));
   if (st) {

@@ -80,6 +80,7 @@ int hr_blas_norm2(const FieldDesc &f, int prec, const void *x, int nrhs, const R
                   cudaStream_t s) {
   dim3 grid(hr_blas_blocks(f.Vh), nrhs * f.nsub);
   if (prec == HR_F64) norm2_kernel<0><<<grid, 256, 0, s>>>(x, f, red, finish);
+  else if (prec == HR_FF) norm2_kernel<3><<<grid, 256, 0, s>>>(x, f, red, finish);
   else if (prec == HR_F32) norm2_kernel<1><<<grid, 256, 0, s>>>(x, f, red, finish);
   else norm2_kernel<2><<<grid, 256, 0, s>>>(x, f, red, finish);
   return hr_check_launch("norm2_kernel");
@@ -117,7 +118,14 @@ int hr_blas_axpby(int px, int py, const void *x, void *y, const FieldDesc &fx, c
   else if (px == 1 && py == 2) AXPBY(1, 2);
   else if (px == 2 && py == 0) AXPBY(2, 0);
   else if (px == 2 && py == 1) AXPBY(2, 1);
-  else AXPBY(2, 2);
+  else if (px == 2 && py == 2) AXPBY(2, 2);
+  // float-float: conversions from / to FP64 and FP32, and updates
+  else if (px == 0 && py == 3) AXPBY(0, 3);
+  else if (px == 3 && py == 0) AXPBY(3, 0);
+  else if (px == 1 && py == 3) AXPBY(1, 3);
+  else if (px == 3 && py == 1) AXPBY(3, 1);
+  else if (px == 3 && py == 3) AXPBY(3, 3);
+  else return HR_ERR_UNSUPPORTED;
 #undef AXPBY
   return hr_check_launch("axpby_kernel");
 }

@@ -94,8 +94,9 @@ __device__ __forceinline__ void ldc(const char *f, int64_t Vh, int d, int64_t i,
 template <int P>
 __device__ __forceinline__ void stc(char *f, int64_t Vh, int64_t i, int c, const cx<typename PT<P>::A> v[4],
                                     float inv) {
-  if (P == 0) st_colour64(f, Vh, i, c, reinterpret_cast<const cx<double> *>(v));
-  else if (P == 1) st_colour32(f, Vh, i, c, reinterpret_cast<const cx<float> *>(v));
+  if constexpr (P == 0) st_colour64(f, Vh, i, c, reinterpret_cast<const cx<double> *>(v));
+  else if constexpr (P == 1) st_colour32(f, Vh, i, c, reinterpret_cast<const cx<float> *>(v));
+  else if constexpr (P == 3) st_colour_ff(f, Vh, i, c, v);
   else {
     cx<float> w[4];
 #pragma unroll
@@ -230,6 +231,7 @@ __device__ __forceinline__ double axpby_sites(const char *xb, char *yb, int64_t 
       for (int q = 0; q < 4; ++q) {
         if (PY == 2) yv[q] = mk(av * (AY)xv[q].x + bv * yv[q].x, av * (AY)xv[q].y + bv * yv[q].y);
         else yv[q] = mk(fma(av, (AY)xv[q].x, bv * yv[q].x), fma(av, (AY)xv[q].y, bv * yv[q].y));
+        if constexpr (PY == 3) yv[q] = mk(ff_norm(yv[q].x), ff_norm(yv[q].y));  // after a cancellation |l| ~ |h|
         s[q] = fma(yv[q].y, yv[q].y, fma(yv[q].x, yv[q].x, s[q]));
       }
       stc<PY>(yb, Vh, i, c, yv, inv);

@@ -14,7 +14,10 @@
 // Mixed precision is defect correction: the FP64 residual r = b - M x is
 // rescaled to unit norm, the inner CG (FP32, or FP16 operator fields with
 // per-site scales and FP32 x, r) reduces it by inner_tol, x += |r| e in FP64,
-// and r is recomputed exactly in FP64, until |r| <= tol |b|.  With an FP16
+// and r is recomputed exactly in FP64, until |r| <= tol |b|.  With
+// outer_prec = HR_FF the outer iterate, b and r are float-float fields and r is
+// recomputed by the float-float operator (about 48 bits, on the FP32 pipes);
+// x is written back in FP64 at exit.  With an FP16
 // inner solver a middle level sits in between: the FP16 CG restarts from FP32
 // true residuals (r32 - M e32, FP32 operator) until the FP32 system has
 // dropped by HR_MID_TOL, and only then is the (expensive on this part) FP64
@@ -256,11 +259,12 @@ static int cg_loop(CgCtx &c, int pr, int pp, void *x, void *r, void *p, void *Ap
   return status;
 }
 
-// r = b - M x (FP64), returns |r|^2 per rhs on the host (w->host S_OUT)
-static int true_residual(CgCtx &c, void *r, const void *b, const void *x, void *Ap, void *t, const FieldDesc &f,
-                         double *rn2) {
+// r = b - M x in precision po (HR_F64 or HR_FF; r, b, x, Ap and t all in it),
+// returns |r|^2 per rhs on the host
+static int true_residual(CgCtx &c, int po, void *r, const void *b, const void *x, void *Ap, void *t,
+                         const FieldDesc &f, double *rn2) {
   hr_cg_work *w = c.lat->cg;
-  HR_TRY(apply_normal(c, HR_F64, Ap, x, t, f, RED_NONE_SKIP, nullptr));
+  HR_TRY(apply_normal(c, po, Ap, x, t, f, RED_NONE_SKIP, nullptr));
   double one[HR_MAX_RHS], zero[HR_MAX_RHS], mone[HR_MAX_RHS];
   for (int q = 0; q < HR_MAX_RHS; ++q) {
     one[q] = 1.0;
@@ -271,10 +275,10 @@ static int true_residual(CgCtx &c, void *r, const void *b, const void *x, void *
   HR_CUDA(cudaMemcpyAsync(S(w, S_B), zero, sizeof(zero), cudaMemcpyHostToDevice, c.s));
   RedArgs red = c.red;
   red.out = S(w, S_OUT);
-  HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+  HR_TRY(hr_blas_axpby(po, po, b, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
   HR_CUDA(cudaMemcpyAsync(S(w, S_A), mone, sizeof(mone), cudaMemcpyHostToDevice, c.s));
   HR_CUDA(cudaMemcpyAsync(S(w, S_B), one, sizeof(one), cudaMemcpyHostToDevice, c.s));
-  HR_TRY(hr_blas_axpby(HR_F64, HR_F64, Ap, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
+  HR_TRY(hr_blas_axpby(po, po, Ap, r, f, f, c.nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
   HR_CUDA(cudaMemcpyAsync(rn2, S(w, S_OUT), sizeof(double) * c.nrhs, cudaMemcpyDeviceToHost, c.s));
   HR_CUDA(cudaStreamSynchronize(c.s));
   return HR_OK;
@@ -342,6 +346,16 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
 
   double bn2[HR_MAX_RHS], rn2[HR_MAX_RHS], v[HR_MAX_RHS];
   int status = HR_OK, iters = 0, outer = 0;
+  // outer residuals in float-float where that operator is built (mixed solves only)
+  HopShape ffs[HR_MAX_SHAPES];
+  const int po = (lo != HR_F64 && prm->outer_prec == HR_FF && !lat->dom &&
+                  hr_hop_shapes(lat->d, lat->is_real, HR_FF, csw != 0.0, nrhs > 1, ffs) > 0)
+                     ? HR_FF
+                     : HR_F64;
+  // the outer iterate and b in precision po: x and b themselves for FP64, else
+  // the FP64 workspace's spare x and p buffers (p is unused by the mixed solve)
+  void *xo = po == HR_FF ? w->f[HR_F64][4] : x;
+  const void *bo = po == HR_FF ? w->f[HR_F64][1] : b;
   const int check_every = prm->check_every > 0 ? prm->check_every : 10;
   const int maxit = prm->maxit > 0 ? prm->maxit : 100000;
   // x = 0, r = b, |b|^2
@@ -356,8 +370,12 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
     HR_TRY(set_scalars(c, S_B, zero));
     RedArgs red = c.red;
     red.out = S(w, S_OUT);
-    HR_TRY(hr_blas_axpby(HR_F64, HR_F64, b, r, f64, f64, nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
+    HR_TRY(hr_blas_axpby(HR_F64, po, b, r, f64, f64, nrhs, S(w, S_A), S(w, S_B), red, 1, c.s));
     HR_CUDA(cudaMemcpyAsync(bn2, S(w, S_OUT), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c.s));
+    if (po == HR_FF) {
+      HR_CUDA(cudaMemcpyAsync(w->f[HR_F64][1], r, bytes64, cudaMemcpyDeviceToDevice, c.s));
+      HR_CUDA(cudaMemsetAsync(xo, 0, bytes64, c.s));
+    }
     HR_CUDA(cudaStreamSynchronize(c.s));
   }
   for (int q = 0; q < nrhs; ++q) rn2[q] = bn2[q];
@@ -374,7 +392,7 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
       iters += done;
       ++outer;
       if (status != HR_OK) break;
-      HR_TRY(true_residual(c, r, b, x, Ap, t, f64, rn2));
+      HR_TRY(true_residual(c, HR_F64, r, b, x, Ap, t, f64, rn2));
       bool ok = true;
       for (int q = 0; q < nrhs; ++q)
         if (!(rn2[q] <= prm->tol * prm->tol * bn2[q])) ok = false;
@@ -424,7 +442,7 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
       HR_TRY(set_scalars(c, S_B, zero));
       RedArgs red = c.red;
       red.out = S(w, S_OUT);
-      HR_TRY(hr_blas_axpby(HR_F64, HR_F32, r, rl, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_TRY(hr_blas_axpby(po, HR_F32, r, rl, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
       HR_TRY(set_scalars(c, S_A, one));
       HR_TRY(hr_blas_axpby(HR_F32, lo, rl, pl, f32, flo, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
       HR_CUDA(cudaMemsetAsync(xl, 0, fb32 * nsub * nrhs, c.s));
@@ -448,7 +466,7 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
         // r32 = rl_initial is gone (rl was iterated); rebuild it from r: r32 = r / |r|
         HR_TRY(set_scalars(c, S_A, a));  // a = 1/|r| still
         HR_TRY(set_scalars(c, S_B, mz));
-        HR_TRY(hr_blas_axpby(HR_F64, HR_F32, r, r32, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+        HR_TRY(hr_blas_axpby(po, HR_F32, r, r32, f64, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
         // e32 = xl
         HR_TRY(set_scalars(c, S_A, mx));
         HR_TRY(hr_blas_axpby(HR_F32, HR_F32, xl, e32, f32, f32, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
@@ -502,8 +520,20 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
       for (int q = 0; q < nrhs; ++q) a[q] = sqrt(rn2[q]);
       HR_TRY(set_scalars(c, S_A, a));
       HR_TRY(set_scalars(c, S_B, one));
-      HR_TRY(hr_blas_axpby(HR_F32, HR_F64, xacc, x, f32, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
-      HR_TRY(true_residual(c, r, b, x, Ap, t, f64, rn2));
+      HR_TRY(hr_blas_axpby(HR_F32, po, xacc, xo, f32, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
+      HR_TRY(true_residual(c, po, r, bo, xo, Ap, t, f64, rn2));
+    }
+    if (po == HR_FF) {  // x = the FP64 value of the float-float iterate
+      double one[HR_MAX_RHS], zero[HR_MAX_RHS];
+      for (int q = 0; q < HR_MAX_RHS; ++q) {
+        one[q] = 1.0;
+        zero[q] = 0.0;
+      }
+      HR_TRY(set_scalars(c, S_A, one));
+      HR_TRY(set_scalars(c, S_B, zero));
+      RedArgs red = c.red;
+      red.out = S(w, S_OUT);
+      HR_TRY(hr_blas_axpby(HR_FF, HR_F64, xo, x, f64, f64, nrhs, S(w, S_A), S(w, S_B), red, 0, c.s));
     }
   }
   HR_CUDA(cudaStreamSynchronize(c.s));

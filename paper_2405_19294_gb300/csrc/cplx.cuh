@@ -51,12 +51,91 @@ __device__ __forceinline__ cx<R> rfma(R r, cx<R> v, cx<R> acc) { return mk(fma(r
 template <typename R>
 __device__ __forceinline__ cx<R> scale(R s, cx<R> a) { return mk(s * a.x, s * a.y); }
 
+// ----------------------------------------------------------- float-float ----
+// A real number as the unevaluated sum h + l of two FP32 numbers (Dekker's
+// double-length arithmetic with Knuth's exact two-sum): about 48 significant
+// bits, the FP32 exponent range, and every operation a handful of FP32
+// instructions.  This part's FP64 pipe runs at about 1/64 of its FP32 pipe, so
+// a stencil in this arithmetic can outrun the same stencil in FP64.
+//
+// Inside a kernel the pairs are not renormalised after every sum (|l| may
+// exceed half an ulp of h, e.g. after a cancellation); products therefore take
+// all four partial products h*h (exactly, as p + fma(h, h, -p)), h*l, l*h and
+// l*l, so the error of every result stays about 2^-47 of the size of its
+// operands.  Stores and norms renormalise.  All operations use the _rn
+// intrinsics, so the compiler neither contracts a product into a following add
+// nor reorders the error terms.
+struct ff {
+  float h, l;
+  ff() = default;
+  __device__ __forceinline__ ff(float x) : h(x), l(0.f) {}
+  __device__ __forceinline__ ff(int x) : h((float)x), l(0.f) {}
+  // the FP64 value to 48 bits: FP64 instructions, so for kernel parameters
+  // and one-off conversions only
+  __device__ __forceinline__ explicit ff(double x) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+  }
+  __device__ __forceinline__ explicit operator double() const { return (double)h + (double)l; }
+  __device__ __forceinline__ explicit operator float() const { return __fadd_rn(h, l); }
+};
+__device__ __forceinline__ ff mkff(float h, float l) {
+  ff r;
+  r.h = h;
+  r.l = l;
+  return r;
+}
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// the same value with |l| at most half an ulp of h
+__device__ __forceinline__ ff ff_norm(ff a) {
+  float s, e;
+  two_sum(a.h, a.l, s, e);
+  return mkff(s, e);
+}
+__device__ __forceinline__ ff operator-(ff a) { return mkff(-a.h, -a.l); }
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return mkff(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.l, b.l, e);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return mkff(p, e);
+}
+// a*b + c
+__device__ __forceinline__ ff fma(ff a, ff b, ff c) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  float s, t;
+  two_sum(p, c.h, s, t);
+  e = __fadd_rn(e, t);
+  e = __fadd_rn(e, c.l);
+  e = __fmaf_rn(a.l, b.l, e);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return mkff(s, e);
+}
+__device__ __forceinline__ bool operator!=(ff a, ff b) { return a.h != b.h || a.l != b.l; }
+
 // ------------------------------------------------------------ precisions ----
-// P = 0 (FP64), 1 (FP32), 2 (FP16); A = accumulation type.
+// P = 0 (FP64), 1 (FP32), 2 (FP16), 3 (float-float); A = accumulation type.
+// Float-float fields, links and clover blocks have the FP64 layouts, each
+// 16-byte chunk holding (re.h, re.l, im.h, im.l) in place of (re, im).
 template <int P> struct PT;
 template <> struct PT<0> { typedef double A; typedef double2 S2; };   // S2: one stored 2-real chunk
 template <> struct PT<1> { typedef float A; typedef float2 S2; };
 template <> struct PT<2> { typedef float A; typedef __half2 S2; };
+template <> struct PT<3> { typedef ff A; typedef float4 S2; };
 
 // 2-real chunk k (link or clover) of site i, converted to the accumulation type
 template <int P>
@@ -76,6 +155,11 @@ __device__ __forceinline__ cx<float> ld2<2>(const void *base, int64_t idx) {
   __half2 h = reinterpret_cast<const __half2 *>(base)[idx];
   float2 v = __half22float2(h);
   return mk(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<ff> ld2<3>(const void *base, int64_t idx) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(base) + idx);
+  return mk(mkff(v.x, v.y), mkff(v.z, v.w));
 }
 
 // the four spin components of colour c of site i of a spinor field
@@ -115,6 +199,15 @@ __device__ __forceinline__ void ld_colour<2>(const void *f, int64_t Vh, int64_t 
   psi[2] = mk(f2.x, f2.y);
   psi[3] = mk(f3.x, f3.y);
 }
+template <>
+__device__ __forceinline__ void ld_colour<3>(const void *f, int64_t Vh, int64_t i, int c, cx<ff> psi[4]) {
+  const float4 *p = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float4 v = __ldg(p + (int64_t)(4 * c + s) * Vh + i);
+    psi[s] = mk(mkff(v.x, v.y), mkff(v.z, v.w));
+  }
+}
 
 // per-site scale of an FP16 field (stored after the d chunk arrays)
 __device__ __forceinline__ const float *f16_scales(const void *f, int64_t Vh, int d) {
@@ -134,6 +227,15 @@ __device__ __forceinline__ void st_colour32(void *f, int64_t Vh, int64_t i, int 
   float4 *p = reinterpret_cast<float4 *>(f);
   p[(int64_t)(2 * c) * Vh + i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
   p[(int64_t)(2 * c + 1) * Vh + i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+// store colour c of a float-float field, each pair renormalised
+__device__ __forceinline__ void st_colour_ff(void *f, int64_t Vh, int64_t i, int c, const cx<ff> v[4]) {
+  float4 *p = reinterpret_cast<float4 *>(f);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const ff x = ff_norm(v[s].x), y = ff_norm(v[s].y);
+    p[(int64_t)(4 * c + s) * Vh + i] = make_float4(x.h, x.l, y.h, y.l);
+  }
 }
 // store colour c of an FP16 field, values already divided by the site scale
 __device__ __forceinline__ void st_colour16(void *f, int64_t Vh, int64_t i, int c, const cx<float> v[4]) {

@@ -356,6 +356,7 @@ int hr_clover_prepare(hr_lattice *lat, double m0) {
   HR_TRY(hr_check_launch("clover_diag_kernel"));
   lat->clover_m0 = m0;
   lat->clover_cached = 1;
+  lat->clover_ff_ok = 0;
   return HR_OK;
 }
 
@@ -422,9 +423,9 @@ extern "C" int hr_export_clover(hr_lattice *lat, double *A_dev, double m0, int i
 
 // ------------------------------------------------------------------ dphi --
 static const void *clover_ptr(const hr_lattice *lat, int prec, bool inverse, int parity) {
-  const int q = prec == HR_F64 ? 0 : 1;
+  const int q = prec == HR_F64 ? 0 : (prec == HR_FF ? 2 : 1);
   const void *base = inverse ? lat->clover_Ainv[q] : lat->clover_A[q];
-  const size_t es = q == 0 ? 16 : 8;
+  const size_t es = q == 1 ? 8 : 16;
   return reinterpret_cast<const char *>(base) + (size_t)parity * 4 * lat->d * lat->d * (size_t)lat->Vh * es;
 }
 
@@ -436,13 +437,14 @@ int hr_dphi_impl(hr_lattice *lat, void *out, const void *in, int parity, double 
 int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw, int prec,
                       int nrhs, int dagger, cudaStream_t st, const double *skip_rr, const double *skip_stop) {
   const bool clover = csw != 0.0;
-  if (clover) HR_TRY(hr_clover_prepare(lat, m0));
+  if (prec == HR_FF) HR_TRY(hr_ff_prepare(lat, clover, m0, st));
+  else if (clover) HR_TRY(hr_clover_prepare(lat, m0));
   const size_t fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
   const double diag = 4.0 + m0;
   HopArgs a;
   memset(&a, 0, sizeof(a));
   a.links = lat->links[prec];
-  a.rlinks = lat->rlinks[prec];
+  a.rlinks = prec == HR_FF ? nullptr : lat->rlinks[prec];
   a.dagger = dagger;
   a.nrhs = nrhs;
   a.skip_rr = skip_rr;
@@ -493,10 +495,11 @@ int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, do
 
 extern "C" int hr_dphi(hr_lattice *lat, void *out, const void *in, int parity, double m0, double csw, int prec,
                        int nrhs, int dagger) {
-  if (!lat || !out || !in || nrhs < 1 || prec < HR_F64 || prec > HR_F16 || parity < HR_EVEN || parity > HR_FULL)
+  if (!lat || !out || !in || nrhs < 1 || prec < HR_F64 || prec > HR_FF || parity < HR_EVEN || parity > HR_FULL)
     return HR_ERR_ARG;
   if (!lat->have_links) return HR_ERR_STATE;
   if (csw != lat->csw) return HR_ERR_ARG;
   if (out == in) return HR_ERR_ARG;
+  if (prec == HR_FF && lat->dom) return HR_ERR_UNSUPPORTED;
   return hr_dphi_impl(lat, out, in, parity, m0, csw, prec, nrhs, dagger, lat->stream);
 }

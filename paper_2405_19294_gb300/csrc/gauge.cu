@@ -403,6 +403,7 @@ extern "C" int hr_represent_links(hr_lattice *lat, const double *U_dev, int reun
   // the rows kernel (no clover) reads its own layout of the same links
   if (csw == 0.0 && !lat->dom && hr_has_rows_shapes(lat->d, lat->is_real)) HR_TRY(hr_rows_links_build(lat, k));
   lat->have_links = 1;
+  lat->ff_links_ok = 0;
   lat->csw = csw;
   lat->clover_cached = 0;
   if (csw != 0.0) HR_TRY(hr_clover_build(lat));

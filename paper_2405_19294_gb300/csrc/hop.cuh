@@ -302,7 +302,7 @@ __device__ __forceinline__ void herm_apply(const void *cl, int64_t Vh, int64_t i
                                            cx<typename PT<P>::A> w[2 * D]) {
   typedef typename PT<P>::A A;
   constexpr int n = 2 * D;
-  constexpr int PC = (P == 0) ? 0 : 1;  // clover storage: FP64 for FP64 fields, else FP32
+  constexpr int PC = (P == 0 || P == 3) ? P : 1;  // clover storage: FP64 / float-float, else FP32
 #pragma unroll
   for (int q = 0; q < D; ++q) {
     const cx<A> dg = ld2<PC>(cl, (int64_t)(off + q) * Vh + i);

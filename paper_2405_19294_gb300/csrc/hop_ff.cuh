@@ -1,0 +1,188 @@
+// Float-float hopping stencil: one site per thread, every real a pair of
+// FP32 numbers (cplx.cuh), for d_R <= 8.  Each hop_ff_*.cu translation unit
+// instantiates some of the (d_R, real) classes (compiled in parallel).
+//
+// The eight hops run as a loop with the direction a run-time value, unlike the
+// fully unrolled FP32 / FP16 / FP64 stencil (hop.cuh): a float-float stencil
+// is about ten times the instructions of an FP32 one, and unrolled over the
+// eight hops it no longer fits the instruction caches (measured: warps stalled
+// about 8 cycles per issued instruction waiting for instructions).  The
+// projection and reconstruction of hop.cuh's compile-time forms become
+// selects on the direction: for direction mu, with sig = -+1 the sign of the
+// hop,
+//   h0 = psi0 - sig X psi_a,   h1 = psi1 + f1 sig X psi_b,
+// a = 2 for mu in {t, z} else 3, b the other of {2, 3}, f1 = -1 for mu in
+// {t, x} else +1, and X = 1 for mu in {t, y}, i for mu in {x, z}; and
+//   acc0 += r0, acc1 += r1, acc2 += g2 sig X r_m, acc3 += g3 sig X r_n,
+// with (m, n) = (0, 1) for mu in {t, z} else (1, 0), g2 = -1 for t else +1,
+// g3 = +1 for x else -1.
+#pragma once
+
+#include "hop.cuh"
+
+// b scaled by f = +-1 (exact), times i when odd
+__device__ __forceinline__ cx<ff> ff_rot(cx<ff> b, float f, bool odd) {
+  const ff bx = odd ? -b.y : b.x, by = odd ? b.x : b.y;
+  return mk(mkff(f * bx.h, f * bx.l), mkff(f * by.h, f * by.l));
+}
+
+template <int D, bool REAL>
+__device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
+  const size_t roff = (size_t)rhs * k.stride;
+  const char *in = reinterpret_cast<const char *>(k.in) + roff;
+  char *out = reinterpret_cast<char *>(k.out) + roff;
+  const int64_t Vh = k.Vh;
+  const int L = k.L, Lh = k.Lh, T = k.T, p = k.p;
+  const Site s = site_of(i, p, L, Lh);
+  const float sg = (float)k.sgn;  // +-1
+  const int64_t slab = (int64_t)k.nch * Vh;
+  const int64_t LLh = (int64_t)L * Lh;
+
+  cx<ff> acc[D][4];
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[c][q] = mk(ff(0), ff(0));
+
+#pragma unroll 1
+  for (int n = 0; n < 8; ++n) {
+    const int mu = n >> 1;
+    const bool back = (n & 1) != 0;
+    // neighbour j of site i along -+mu (as in hop.cuh)
+    const int cc = mu == 0 ? s.t : (mu == 1 ? s.x : (mu == 2 ? s.y : s.z));
+    const int E = mu == 0 ? T : L;
+    const int cn = back ? (cc == 0 ? E - 1 : cc - 1) : (cc + 1 == E ? 0 : cc + 1);
+    const int64_t st = mu == 0 ? (int64_t)L * LLh : (mu == 2 ? (int64_t)Lh : LLh);
+    const int64_t j = mu == 1 ? i - (cc >> 1) + (cn >> 1) : i + (int64_t)(cn - cc) * st;
+    // forward: U_mu(x) from the slot of parity p at i; backward: U_mu(x - mu)^+ at j
+    const char *lk = reinterpret_cast<const char *>(k.links) + (size_t)(((back ? 1 - p : p) * 4 + mu) * slab) * 16u;
+    const int64_t li = back ? j : i;
+    const float sig = back ? sg : -sg;
+    const bool odd = (mu & 1) != 0;
+    const bool tz = mu == 0 || mu == 3;
+    const float f1 = mu < 2 ? -sig : sig;
+    const float g2 = mu == 0 ? -sig : sig, g3 = mu == 1 ? sig : -sig;
+
+    cx<ff> h0[D], h1[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      cx<ff> psi[4];
+      ld_colour<3>(in, Vh, j, c, psi);
+      const cx<ff> pa = tz ? psi[2] : psi[3], pb = tz ? psi[3] : psi[2];
+      h0[c] = psi[0] + ff_rot(pa, -sig, odd);
+      h1[c] = psi[1] + ff_rot(pb, f1, odd);
+    }
+    if constexpr (REAL) {
+      // real links: chunk e >> 1, half e & 1 of entry e = a D + c (U^T backward)
+      constexpr int NC = (D * D + 1) / 2;
+      cx<ff> u[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) u[q] = ld2<3>(lk, (int64_t)q * Vh + li);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        cx<ff> r0 = mk(ff(0), ff(0)), r1 = mk(ff(0), ff(0));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const int ef = a * D + c, eb = c * D + a;
+          const ff uf = (ef & 1) ? u[ef >> 1].y : u[ef >> 1].x;
+          const ff ub = (eb & 1) ? u[eb >> 1].y : u[eb >> 1].x;
+          const ff ue = back ? ub : uf;
+          r0 = rfma(ue, h0[c], r0);
+          r1 = rfma(ue, h1[c], r1);
+        }
+        const cx<ff> rm = tz ? r0 : r1, rn = tz ? r1 : r0;
+        acc[a][0] = acc[a][0] + r0;
+        acc[a][1] = acc[a][1] + r1;
+        acc[a][2] = acc[a][2] + ff_rot(rm, g2, odd);
+        acc[a][3] = acc[a][3] + ff_rot(rn, g3, odd);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        // row a of U, or column a of U conjugated (U^+), loaded before the products
+        cx<ff> ur[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          ur[c] = ld2<3>(lk, (int64_t)(back ? c * D + a : a * D + c) * Vh + li);
+          if (back) ur[c].y = -ur[c].y;
+        }
+        cx<ff> r0 = mk(ff(0), ff(0)), r1 = mk(ff(0), ff(0));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          r0 = cfma(ur[c], h0[c], r0);
+          r1 = cfma(ur[c], h1[c], r1);
+        }
+        const cx<ff> rm = tz ? r0 : r1, rn = tz ? r1 : r0;
+        acc[a][0] = acc[a][0] + r0;
+        acc[a][1] = acc[a][1] + r1;
+        acc[a][2] = acc[a][2] + ff_rot(rm, g2, odd);
+        acc[a][3] = acc[a][3] + ff_rot(rn, g3, odd);
+      }
+    }
+  }
+
+  // ---- epilogue (hop.cuh's, in float-float) ----
+  const ff coef(k.coef);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[c][q] = scale(coef, acc[c][q]);
+  if (k.mode == HOP_SCALED) {
+    if (k.clover) clover_apply<D, 3>(k.clover, Vh, i, acc);
+  } else {
+    const char *self = reinterpret_cast<const char *>(k.self) + roff;
+    cx<ff> sv[D][4];
+#pragma unroll
+    for (int c = 0; c < D; ++c) ld_colour<3>(self, Vh, i, c, sv[c]);
+    if (k.clover) {
+      clover_apply<D, 3>(k.clover, Vh, i, sv);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[c][q] = acc[c][q] + sv[c][q];
+    } else {
+      const ff dg(k.diag);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[c][q] = axpy_r(dg, sv[c][q], acc[c][q]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) st_colour_ff(out, Vh, i, c, acc[c]);
+}
+
+template <int D, bool REAL, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) hop_ff_kernel(HopK k, SkipK sk) {
+  pdl_start();
+  int64_t tile;
+  int rhs;
+  block_tile(k, tile, rhs);
+  if (rhs_done(sk, rhs)) return;
+  const int64_t i = tile * blockDim.x + threadIdx.x;
+  if (i < k.Vh) hop_site_ff<D, REAL>(k, i, rhs);
+}
+
+// (d_R, real links, launcher name) of every class built in float-float
+#define HR_FF_CLASSES(X)                                                                               \
+  X(2, false, hr_ff_c2) X(3, false, hr_ff_c3) X(3, true, hr_ff_r3) X(4, false, hr_ff_c4)             \
+  X(5, false, hr_ff_c5) X(6, false, hr_ff_c6) X(7, false, hr_ff_c7) X(8, false, hr_ff_c8)             \
+  X(8, true, hr_ff_r8)
+
+// register-budget variant 1 (128 threads x 3 blocks, about 168 registers)
+// only where it does not spill: d_R <= 3
+template <int D, bool REAL>
+static void launch_site_ff(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {
+  if constexpr (D <= 3) {
+    if (variant == 1) {
+      launch_pdl(hop_ff_kernel<D, REAL, 128, 3>, k, sk, grid, bs, st, pdl);
+      return;
+    }
+  }
+  launch_pdl(hop_ff_kernel<D, REAL, 256, 1>, k, sk, grid, bs, st, pdl);
+}
+
+#define HR_FF_DEFINE(DD, RE, NAME)                                                                   \
+  void NAME(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {   \
+    launch_site_ff<DD, RE>(k, sk, grid, bs, variant, st, pdl);                                       \
+  }

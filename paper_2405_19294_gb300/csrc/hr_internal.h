@@ -40,7 +40,8 @@ struct hr_lattice {
   cudaStream_t stream;
   int device;
   int nch_link;          // 2-real chunks per link
-  void *links[3];        // per hr_prec
+  void *links[4];        // per hr_prec (HR_FF: made from the FP64 links on first use)
+  int ff_links_ok;       // links[HR_FF] matches links[HR_F64]
   int have_links;
   void *rlinks[3];       // per hr_prec: rows-kernel link layout (see hr_rows_nch), or null
   int dom;               // 1: a time slab [t0, t0 + T) of a T_global lattice (faces via halo buffers)
@@ -52,8 +53,9 @@ struct hr_lattice {
   double clover_m0;      // m0 of the cached A and A^{-1} below
   int clover_cached;
   int clover_exp;         // 1: A = (4+m0) exp(term / (4+m0)) (exponentiated clover)
-  void *clover_A[2];     // FP64, FP32 packed A = (4+m0) + term
-  void *clover_Ainv[2];  // FP64, FP32 packed A^{-1}
+  void *clover_A[3];     // FP64, FP32, float-float packed A = (4+m0) + term
+  void *clover_Ainv[3];  // FP64, FP32, float-float packed A^{-1}
+  int clover_ff_ok;      // clover_A[2], clover_Ainv[2] match the FP64 blocks
   void *tmp;             // Schur intermediate spinor (other parity)
   size_t tmp_bytes;
   int *dev_err;          // latched device error word
@@ -116,14 +118,16 @@ static inline HrGeom hr_geom(const hr_lattice *lat) {
 
 // chunks and bytes of one single-parity, single-rhs spinor field
 static inline int hr_spinor_chunks(int d, int prec) {
-  return prec == HR_F64 ? 4 * d : (prec == HR_F32 ? 2 * d : d);
+  return (prec == HR_F64 || prec == HR_FF) ? 4 * d : (prec == HR_F32 ? 2 * d : d);
 }
 static inline size_t hr_spinor_field_bytes(int64_t Vh, int d, int prec) {
   size_t b = (size_t)hr_spinor_chunks(d, prec) * 16u * (size_t)Vh;
   if (prec == HR_F16) b += 4u * (size_t)Vh;
   return (b + 255u) & ~(size_t)255u;
 }
-static inline size_t hr_real_size(int prec) { return prec == HR_F64 ? 8 : (prec == HR_F32 ? 4 : 2); }
+static inline size_t hr_real_size(int prec) {
+  return (prec == HR_F64 || prec == HR_FF) ? 8 : (prec == HR_F32 ? 4 : 2);
+}
 
 // ------------------------------------------------------------ launchers ----
 // Hopping kernel epilogue modes.
@@ -230,6 +234,11 @@ int hr_launch_hop(const hr_lattice *lat, int prec, const HopArgs &a, cudaStream_
 int hr_launch_hop_f64(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
 int hr_launch_hop_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+int hr_launch_hop_ff(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh);
+// hop_ff.cu: float-float copies of FP64 arrays, and of the links (and of the
+// clover blocks at m0) of a lattice, made on stream st when missing or stale
+int hr_f64_to_ff(void *out, const void *in, size_t nreal, cudaStream_t s);
+int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st);
 // tensor-core multi-rhs kernel (complex d_R = 3 ... 6), FP32 (FP16 pairs) / FP16
 int hr_launch_hop_tc_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
 int hr_launch_hop_tc_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);

@@ -184,13 +184,11 @@ extern "C" int hr_lattice_destroy(hr_lattice *lat) {
   if (!lat) return HR_ERR_ARG;
   cudaDeviceSynchronize();  // the solver streams too: nothing may still use what is freed below
   hr_bicgstab_forget(lat);
-  for (int p = 0; p < 3; ++p) {
-    hr_dev_free(lat->links[p]);
-    hr_dev_free(lat->rlinks[p]);
-  }
+  for (int p = 0; p < 3; ++p) hr_dev_free(lat->rlinks[p]);
+  for (int p = 0; p < 4; ++p) hr_dev_free(lat->links[p]);
   for (int b = 0; b < 4; ++b) hr_dev_free(lat->halo[b]);
   hr_dev_free(lat->clover_term);
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     hr_dev_free(lat->clover_A[p]);
     hr_dev_free(lat->clover_Ainv[p]);
   }
@@ -237,7 +235,7 @@ extern "C" int hr_lattice_info(const hr_lattice *lat, hr_info *info) {
 }
 
 extern "C" int hr_field_bytes(const hr_lattice *lat, int parity, int prec, int nrhs, size_t *bytes) {
-  if (!lat || !bytes || nrhs < 1 || prec < HR_F64 || prec > HR_F16 || parity < HR_EVEN || parity > HR_FULL)
+  if (!lat || !bytes || nrhs < 1 || prec < HR_F64 || prec > HR_FF || parity < HR_EVEN || parity > HR_FULL)
     return HR_ERR_ARG;
   const size_t fb = hr_spinor_field_bytes(lat->Vh, lat->d, prec);
   *bytes = fb * (parity == HR_FULL ? 2u : 1u) * (size_t)nrhs;
@@ -280,6 +278,13 @@ __global__ void pack_kernel(void *internal, const double *canon, PackK k) {
     for (int c = 0; c < d; ++c)
       for (int sp = 0; sp < 4; ++sp)
         q[(int64_t)(4 * c + sp) * Vh + i] = make_double2(src[2 * (sp * d + c)], src[2 * (sp * d + c) + 1]);
+  } else if (P == 3) {
+    float4 *q = reinterpret_cast<float4 *>(f);
+    for (int c = 0; c < d; ++c)
+      for (int sp = 0; sp < 4; ++sp) {
+        const ff re(src[2 * (sp * d + c)]), im(src[2 * (sp * d + c) + 1]);
+        q[(int64_t)(4 * c + sp) * Vh + i] = make_float4(re.h, re.l, im.h, im.l);
+      }
   } else if (P == 1) {
     float4 *q = reinterpret_cast<float4 *>(f);
     for (int c = 0; c < d; ++c)
@@ -324,6 +329,14 @@ __global__ void unpack_kernel(double *canon, const void *internal, PackK k) {
         double2 v = q[(int64_t)(4 * c + sp) * Vh + i];
         dst[2 * (sp * d + c)] = v.x;
         dst[2 * (sp * d + c) + 1] = v.y;
+      }
+  } else if (P == 3) {
+    const float4 *q = reinterpret_cast<const float4 *>(f);
+    for (int c = 0; c < d; ++c)
+      for (int sp = 0; sp < 4; ++sp) {
+        float4 v = q[(int64_t)(4 * c + sp) * Vh + i];
+        dst[2 * (sp * d + c)] = (double)v.x + (double)v.y;
+        dst[2 * (sp * d + c) + 1] = (double)v.z + (double)v.w;
       }
   } else if (P == 1) {
     const float4 *q = reinterpret_cast<const float4 *>(f);
@@ -376,7 +389,7 @@ static int resolve_canonical(const void *p, const void **dev) {
 static int pack_common(hr_lattice *lat, void *internal, double *canon_w, const double *canon_r, int parity,
                        int prec, int nrhs, bool pack) {
   if (!lat || !internal || !(pack ? (const void *)canon_r : (const void *)canon_w) || nrhs < 1 ||
-      prec < HR_F64 || prec > HR_F16 || parity < HR_EVEN || parity > HR_FULL)
+      prec < HR_F64 || prec > HR_FF || parity < HR_EVEN || parity > HR_FULL)
     return HR_ERR_ARG;
   {
     const void *dev = nullptr;
@@ -400,10 +413,12 @@ static int pack_common(hr_lattice *lat, void *internal, double *canon_w, const d
     k.poff = (parity == HR_FULL && p == 1) ? fb : 0;
     if (pack) {
       if (prec == HR_F64) pack_kernel<0><<<grid, 128, 0, lat->stream>>>(internal, canon_r, k);
+      else if (prec == HR_FF) pack_kernel<3><<<grid, 128, 0, lat->stream>>>(internal, canon_r, k);
       else if (prec == HR_F32) pack_kernel<1><<<grid, 128, 0, lat->stream>>>(internal, canon_r, k);
       else pack_kernel<2><<<grid, 128, 0, lat->stream>>>(internal, canon_r, k);
     } else {
       if (prec == HR_F64) unpack_kernel<0><<<grid, 128, 0, lat->stream>>>(canon_w, internal, k);
+      else if (prec == HR_FF) unpack_kernel<3><<<grid, 128, 0, lat->stream>>>(canon_w, internal, k);
       else if (prec == HR_F32) unpack_kernel<1><<<grid, 128, 0, lat->stream>>>(canon_w, internal, k);
       else unpack_kernel<2><<<grid, 128, 0, lat->stream>>>(canon_w, internal, k);
     }

@@ -22,6 +22,18 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
   int n = 0;
   const bool site = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 8);
   const bool site_mrhs = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
+  if (prec == HR_FF) {
+    // float-float: its site kernel (hop_ff.cuh), compiler's register choice
+    // or (d_R <= 3, where it does not spill) the high budget
+    if (!site) return 0;
+    const int bss[4] = {64, 128, 32, 256};
+    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0, 0};
+    if (d <= 3) {
+      out[n++] = HopShape{0, 64, 1, 0};
+      out[n++] = HopShape{0, 128, 1, 0};
+    }
+    return n;
+  }
   if (multi_rhs && hr_has_tc_mrhs(d, is_real, prec))
     out[n++] = HopShape{0, 0, 0, HR_TC_MRHS + 16};  // link products of all rhs as MMA tiles
   if (site_mrhs && multi_rhs) {
@@ -76,6 +88,7 @@ static int launch_shape(const hr_lattice *lat, int prec, const HopArgs &a, cudaS
     case HR_F64: return hr_launch_hop_f64(lat, a, s, sh);
     case HR_F32: return hr_launch_hop_f32(lat, a, s, sh);
     case HR_F16: return hr_launch_hop_f16(lat, a, s, sh);
+    case HR_FF: return hr_launch_hop_ff(lat, a, s, sh);
   }
   return HR_ERR_ARG;
 }
@@ -164,7 +177,7 @@ extern "C" int hr_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clo
 
 // Candidate shapes of this lattice's hop, encoded as hr_tuned_shape reports them.
 extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs, int clover, int *out, int max) {
-  if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
+  if (!lat || !out || max < 1 || prec < HR_F64 || prec > HR_FF || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
   const int n = lattice_shapes(lat, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n && k < max; ++k)
@@ -175,7 +188,7 @@ extern "C" int hr_hop_shape_candidates(const hr_lattice *lat, int prec, int nrhs
 // Pin the shape used for (prec, nrhs, clover) on this lattice's size class,
 // bypassing the timing; the shape must be one of the candidates.
 extern "C" int hr_set_tuned_shape(const hr_lattice *lat, int prec, int nrhs, int clover, int shape) {
-  if (!lat || prec < HR_F64 || prec > HR_F16 || nrhs < 1) return HR_ERR_ARG;
+  if (!lat || prec < HR_F64 || prec > HR_FF || nrhs < 1) return HR_ERR_ARG;
   HopShape shapes[HR_MAX_SHAPES];
   const int n = lattice_shapes(lat, prec, clover, nrhs > 1, shapes);
   for (int k = 0; k < n; ++k)

@@ -23,8 +23,8 @@ _lib = C.CDLL(LIB_PATH)
 FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
 REP = {"fund": FUND, "adj": ADJ, "sym": SYM, "asym": ASYM}
 EVEN, ODD, FULL = 0, 1, 2
-F64, F32, F16 = 0, 1, 2
-PREC = {"f64": F64, "f32": F32, "f16": F16}
+F64, F32, F16, FF = 0, 1, 2, 3  # FF: float-float (hi + lo FP32 pairs in the FP64 field layout)
+PREC = {"f64": F64, "f32": F32, "f16": F16, "ff": FF}
 
 
 class hr_info(C.Structure):
@@ -35,7 +35,8 @@ class hr_info(C.Structure):
 
 class hr_cg_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_prec", C.c_int),
-                ("inner_tol", C.c_double), ("nrhs", C.c_int), ("check_every", C.c_int)]
+                ("inner_tol", C.c_double), ("nrhs", C.c_int), ("check_every", C.c_int),
+                ("outer_prec", C.c_int)]
 
 
 class hr_cg_stats(C.Structure):
@@ -275,11 +276,12 @@ class Lattice:
 
     def cg_solve(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
                  inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,
-                 raise_on_error: bool = True):
-        """Solve Dhat^+ Dhat x = b (D^+ D for FULL) to a true FP64 relative residual tol: plain FP64
-        CG, or FP64 defect correction around an FP32 / FP16 inner CG (hr_cg_solve).  Returns the
-        status and statistics; raises HrError on failure unless raise_on_error is False."""
-        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every)
+                 raise_on_error: bool = True, outer_prec: int = FF):
+        """Solve Dhat^+ Dhat x = b (D^+ D for FULL) to a true relative residual tol: plain FP64
+        CG, or defect correction around an FP32 / FP16 inner CG whose outer residuals run in
+        outer_prec (F64, or FF: float-float) (hr_cg_solve).  Returns the status and statistics;
+        raises HrError on failure unless raise_on_error is False."""
+        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every, outer_prec)
         st = hr_cg_stats()
         rc = _lib.hr_cg_solve(self._h, _ptr(x), _ptr(b), parity, m0, csw, C.byref(prm), C.byref(st))
         if rc != 0 and raise_on_error:
@@ -383,8 +385,10 @@ class Batch:
 
 def _bicgstab(self, x, b, parity: int, m0: float, csw: float, tol: float, inner_prec: int = F64,
               inner_tol: float = 0.0, nrhs: int = 1, maxit: int = 100000, check_every: int = 10,
-              raise_on_error: bool = True):
-    prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every)
+              raise_on_error: bool = True, outer_prec: int = FF):
+    """BiCGstab on Dhat (D for FULL) to a true relative residual tol: plain FP64, or defect
+    correction around an FP32 inner BiCGstab with outer residuals in outer_prec (hr_bicgstab_solve)."""
+    prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, nrhs, check_every, outer_prec)
     st = hr_cg_stats()
     rc = _lib.hr_bicgstab_solve(self._h, _ptr(x), _ptr(b), parity, m0, csw, C.byref(prm), C.byref(st))
     if rc != 0 and raise_on_error:
