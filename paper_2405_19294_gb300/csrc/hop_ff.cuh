@@ -127,26 +127,53 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
   for (int c = 0; c < D; ++c)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[c][q] = scale(coef, acc[c][q]);
-  if (k.mode == HOP_SCALED) {
-    if (k.clover) clover_apply<D, 3>(k.clover, Vh, i, acc);
-  } else {
+  const bool scaled = k.mode == HOP_SCALED;
+  cx<ff> sv[D][4];
+  if (!scaled) {
     const char *self = reinterpret_cast<const char *>(k.self) + roff;
-    cx<ff> sv[D][4];
 #pragma unroll
     for (int c = 0; c < D; ++c) ld_colour<3>(self, Vh, i, c, sv[c]);
-    if (k.clover) {
-      clover_apply<D, 3>(k.clover, Vh, i, sv);
+  }
+  if (k.clover) {
+    // one copy of the block products for both modes: A^{-1} acc (scaled) or
+    // A self (self), each chiral block in turn (loops kept, as above, so that
+    // the code fits the instruction caches)
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (!scaled) {
+          const cx<ff> t = acc[c][q];
+          acc[c][q] = sv[c][q];
+          sv[c][q] = t;
+        }
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+      cx<ff> v[2 * D], w[2 * D];
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[s2 * D + c] = b ? acc[c][2 + s2] : acc[c][s2];
+      herm_apply<D, 3>(k.clover, Vh, i, b * 2 * D * D, v, w);
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          if (b) acc[c][2 + s2] = w[s2 * D + c];
+          else acc[c][s2] = w[s2 * D + c];
+        }
+    }
+    if (!scaled)
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[c][q] = acc[c][q] + sv[c][q];
-    } else {
-      const ff dg(k.diag);
+  } else if (!scaled) {
+    const ff dg(k.diag);
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+    for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[c][q] = axpy_r(dg, sv[c][q], acc[c][q]);
-    }
+      for (int q = 0; q < 4; ++q) acc[c][q] = axpy_r(dg, sv[c][q], acc[c][q]);
   }
 #pragma unroll
   for (int c = 0; c < D; ++c) st_colour_ff(out, Vh, i, c, acc[c]);
