@@ -65,9 +65,9 @@ typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2 } hr_parity;
  * layout with each 16-byte chunk (re.hi, re.lo, im.hi, im.lo); the FP64-accurate
  * operator of the mixed solvers' outer residuals, for a part whose FP64 units
  * run at a small fraction of its FP32 rate.  Accepted by hr_field_bytes,
- * hr_pack_spinor / hr_unpack_spinor, hr_dphi (d_R <= 8 classes of the
- * one-site-per-thread kernel, whole lattices), the shape calls, and
- * hr_cg_params.outer_prec. */
+ * hr_pack_spinor / hr_unpack_spinor, hr_dphi (whole lattices: every class
+ * without clover, and with clover the d_R <= 8 classes), the shape calls,
+ * and hr_cg_params.outer_prec. */
 typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2, HR_FF = 3 } hr_prec;
 
 typedef enum {
@@ -100,8 +100,8 @@ typedef struct {
   int nrhs;          /* number of right-hand sides stored back to back */
   int check_every;   /* inner iterations between residual checks on the host */
   int outer_prec;    /* mixed hr_cg_solve / hr_bicgstab_solve: arithmetic of the outer
-                        residual, HR_F64 (0) or HR_FF (float-float; where the class
-                        has no float-float kernel FP64 is used).  Ignored elsewhere */
+                        residual, HR_F64 (0) or HR_FF (float-float; time slabs use
+                        FP64).  Ignored elsewhere */
 } hr_cg_params;
 
 typedef struct {

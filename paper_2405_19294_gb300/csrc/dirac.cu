@@ -444,7 +444,7 @@ int hr_dphi_impl_skip(hr_lattice *lat, void *out, const void *in, int parity, do
   HopArgs a;
   memset(&a, 0, sizeof(a));
   a.links = lat->links[prec];
-  a.rlinks = prec == HR_FF ? nullptr : lat->rlinks[prec];
+  a.rlinks = lat->rlinks[prec];
   a.dagger = dagger;
   a.nrhs = nrhs;
   a.skip_rr = skip_rr;

@@ -355,8 +355,7 @@ __global__ void rows_links_kernel(void *r64, void *r32, void *r16, const void *l
 }
 
 // 16 matrices of hr_rows_nch chunk rows, then HR_ROWS_SLACK zeroed chunk rows
-// that the rows kernel's last column batch may read past the last matrix.
-#define HR_ROWS_SLACK 16
+// (hr_internal.h)
 static int hr_rows_links_build(hr_lattice *lat, const RepK &k) {
   const size_t nrows = (size_t)16 * hr_rows_nch(lat->d, lat->is_real);
   const size_t es[3] = {16, 8, 4};

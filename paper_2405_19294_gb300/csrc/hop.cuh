@@ -458,8 +458,9 @@ __device__ __forceinline__ void hop_site(const HopK &k, int64_t i, int rhs) {
 
 // Register budget variants (the autotuner picks one with the block size):
 // MAXT x MINB = 256 x 1 (compiler's choice), 128 x 3 (up to ~170 registers: more
-// loads in flight per thread), 64 x 12 (at most ~85 registers: more warps) and
-// 128 x 4 (at most 128 registers, between the two).
+// loads in flight per thread), 64 x 12 (at most ~85 registers: more warps),
+// 128 x 4 (at most 128 registers, between the two), and variant 4: the budget
+// of 1 as a one-wave PERSIST launch (FP32; 1-2 % faster on 24^3 x 48).
 // Programmatic dependent launch: every block lets the next kernel of the
 // stream start launching, and waits for the previous kernel's results (it
 // reads the fields that kernel wrote) before anything else; both are no-ops
@@ -469,15 +470,30 @@ __device__ __forceinline__ void pdl_start() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false>
+// PERSIST: a grid of at most one wave of resident blocks, each block taking
+// work items (tile, rhs) blockIdx.x, + gridDim.x, ... (the launcher sizes the
+// grid so that every block gets the same number of items): no partly filled
+// last wave, which on small lattices leaves SMs idle for a sizeable part of
+// a launch of a few tens of microseconds.
+template <int D, bool REAL, int P, int MAXT, int MINB, bool MASK = false, bool PERSIST = false>
 __global__ void __launch_bounds__(MAXT, MINB) hop_kernel(HopK k, SkipK sk) {
   pdl_start();
-  int64_t tile;
-  int rhs;
-  block_tile(k, tile, rhs);
-  if (rhs_done(sk, rhs)) return;
-  const int64_t i = tile * blockDim.x + threadIdx.x;
-  if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
+  if constexpr (PERSIST) {
+    const int64_t nwork = ((k.Vh + blockDim.x - 1) / blockDim.x) * k.nrhs;
+    for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+      const int rhs = (int)(w % k.nrhs);
+      if (rhs_done(sk, rhs)) continue;
+      const int64_t i = (w / k.nrhs) * blockDim.x + threadIdx.x;
+      if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
+    }
+  } else {
+    int64_t tile;
+    int rhs;
+    block_tile(k, tile, rhs);
+    if (rhs_done(sk, rhs)) return;
+    const int64_t i = tile * blockDim.x + threadIdx.x;
+    if (i < k.Vh) hop_site<D, REAL, P, MASK>(k, i, rhs);
+  }
 }
 
 // Persistent multi-lattice form: every block walks the work list (lattice,
@@ -541,17 +557,55 @@ static void launch_pdl(Kern kern, const HopK &k, SkipK sk, dim3 grid, int bs, cu
   cudaLaunchKernelEx(&cfg, kern, k, sk);
 }
 
+// Grid of a PERSIST launch for `nwork` items: the fewest full waves of
+// resident blocks, spread so that every block gets the same number of items
+// (within one).  Resident blocks per SM are looked up once per kernel, block
+// size and device.
+template <typename Kern>
+static dim3 persist_grid(Kern kern, int bs, unsigned nwork) {
+  static int cache[8][9] = {};  // [device][bs / 32], bs = 32 ... 256
+  static int sms_of[8] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int b = bs / 32;
+  int per_sm = 1, sms = 1;
+  if (dev >= 0 && dev < 8 && b >= 1 && b <= 8) {
+    if (!cache[dev][b]) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, bs, 0) != cudaSuccess || n < 1) n = 1;
+      cache[dev][b] = n;
+    }
+    if (!sms_of[dev]) {
+      int n = 0;
+      if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+      sms_of[dev] = n;
+    }
+    per_sm = cache[dev][b];
+    sms = sms_of[dev];
+  }
+  const unsigned cap = (unsigned)(per_sm * sms);
+  const unsigned waves = (nwork + cap - 1) / cap;
+  return dim3(waves ? (nwork + waves - 1) / waves : 1u);
+}
+
 template <int D, bool REAL, int P>
 static void launch_site(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {
   if (k.tmask) launch_pdl(hop_kernel<D, REAL, P, 256, 1, true>, k, sk, grid, bs, st, pdl);  // time-slab bulk pass
   else if (variant == 1) launch_pdl(hop_kernel<D, REAL, P, 128, 3>, k, sk, grid, bs, st, pdl);
   else if (variant == 2) launch_pdl(hop_kernel<D, REAL, P, 64, 12>, k, sk, grid, bs, st, pdl);
   else if (variant == 3) launch_pdl(hop_kernel<D, REAL, P, 128, 4>, k, sk, grid, bs, st, pdl);
-  else launch_pdl(hop_kernel<D, REAL, P, 256, 1>, k, sk, grid, bs, st, pdl);
+  else if (variant == 4) {
+    // one wave of resident blocks at the budget of variant 1 (FP32 only: on
+    // FP16 fields it measured 5-20 % slower than the ordinary grid)
+    if constexpr (P == 1) {
+      auto kern = hop_kernel<D, REAL, P, 128, 3, false, true>;
+      launch_pdl(kern, k, sk, persist_grid(kern, bs, grid.x), bs, st, pdl);
+    }
+  } else launch_pdl(hop_kernel<D, REAL, P, 256, 1>, k, sk, grid, bs, st, pdl);
 }
 
 // Launch the site-per-thread kernel for (D, REAL) of precision P with `bs`
-// threads per block and register-budget variant 0/1/2 (the autotuner picks).
+// threads per block and register-budget variant 0 ... 4 (the autotuner picks).
 template <int P>
 int hop_dispatch(const hr_lattice *lat, const HopArgs &a, cudaStream_t st, int bs, int variant) {
   const HopK k = make_hopk(lat, a);

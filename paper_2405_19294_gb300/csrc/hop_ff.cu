@@ -1,6 +1,7 @@
 // Float-float operator: the conversions that give it its links and clover
 // blocks, and the dispatch over the per-class instantiations (hop_ff_*.cu) of
-// its one-site-per-thread hopping kernel (hop_ff.cuh), d_R <= 8.
+// its one-site-per-thread hopping kernel (hop_ff.cuh), d_R <= 8, and of the
+// rows kernel (hop_rows.cuh) for the larger representations.
 //
 // The float-float operator is the FP64-accurate Dhat of the mixed solvers'
 // outer residuals (Sec. 3.3): the FP64 kernel's stencil with every real a pair
@@ -31,6 +32,11 @@ int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st) {
     const size_t nreal = (size_t)2 * 4 * lat->nch_link * (size_t)lat->Vh * 2;
     if (!lat->links[HR_FF]) HR_TRY(hr_dev_alloc(&lat->links[HR_FF], nreal * 8));
     HR_TRY(hr_f64_to_ff(lat->links[HR_FF], lat->links[HR_F64], nreal, st));
+    if (lat->rlinks[HR_F64]) {  // the rows kernel's layout, slack rows included
+      const size_t nr = ((size_t)16 * hr_rows_nch(lat->d, lat->is_real) + HR_ROWS_SLACK) * (size_t)lat->Vh * 2;
+      if (!lat->rlinks[HR_FF]) HR_TRY(hr_dev_alloc(&lat->rlinks[HR_FF], nr * 8));
+      HR_TRY(hr_f64_to_ff(lat->rlinks[HR_FF], lat->rlinks[HR_F64], nr, st));
+    }
     lat->ff_links_ok = 1;
   }
   if (clover) {
@@ -56,7 +62,10 @@ int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st) {
 HR_FF_CLASSES(HR_FF_CLASS)
 #undef HR_FF_CLASS
 
+int hr_launch_hop_ff_rows(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int rows);
+
 int hr_launch_hop_ff(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, HopShape sh) {
+  if (sh.rows && !sh.mrhs && !sh.split_g && !a.tmask) return hr_launch_hop_ff_rows(lat, a, s, sh.rows);
   if (sh.mrhs || sh.rows || sh.split_g || a.tmask || (sh.regs != 0 && sh.regs != 1)) return HR_ERR_UNSUPPORTED;
   const HopK k = make_hopk(lat, a);
   const SkipK sk = make_skipk(a);

@@ -25,7 +25,9 @@
 // neighbour suffices: a warp that writes the buffer of neighbour n+2 has
 // passed the barrier of n+1, which every warp reaches only after it has
 // finished reading neighbour n.  No clover epilogue (the clover term is built
-// for d_R <= 8, where the site kernel is used).
+// for d_R <= 8, where the site kernel is used).  Also built in float-float
+// (P = 3) for the mixed solvers' outer residuals: the direction already is a
+// run-time loop variable, so the code stays within the instruction caches.
 #pragma once
 
 #include "hop.cuh"
@@ -202,7 +204,7 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
   const Site s = site_of(ii, p, L, Lh);
   const A sg = (A)k.sgn;
   const int64_t slab = (int64_t)G::NCH * Vh;  // chunks per [p][n] matrix slot
-  const size_t es = (P == 0) ? 16 : (P == 1 ? 8 : 4);
+  const size_t es = (P == 0 || P == 3) ? 16 : (P == 1 ? 8 : 4);
   const float *isc = (P == 2) ? f16_scales(in, Vh, D) : nullptr;
   int ar[R];  // this warp's rows, clamped to the last one
 #pragma unroll
@@ -339,7 +341,7 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
       }
     }
   }
-  if (P == 2) {
+  if constexpr (P == 2) {
     // per-site maximum over all D colours: this warp's rows, then across warps
     float *red = reinterpret_cast<float *>(smem + (size_t)2 * 2 * DC * 32 * sizeof(cx<A>));
     float m = 0.f;
@@ -372,7 +374,8 @@ __device__ __forceinline__ void hop_rows_tile(const HopK &k, int64_t tile, int r
     for (int r = 0; r < R; ++r) {
       const int c = a0 + r;
       if (c < D) {
-        if (P == 0) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[r]));
+        if constexpr (P == 0) st_colour64(out, Vh, i, c, reinterpret_cast<const cx<double> *>(acc[r]));
+        else if constexpr (P == 3) st_colour_ff(out, Vh, i, c, acc[r]);
         else st_colour32(out, Vh, i, c, reinterpret_cast<const cx<float> *>(acc[r]));
       }
     }

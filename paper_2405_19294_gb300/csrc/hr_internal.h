@@ -43,7 +43,7 @@ struct hr_lattice {
   void *links[4];        // per hr_prec (HR_FF: made from the FP64 links on first use)
   int ff_links_ok;       // links[HR_FF] matches links[HR_F64]
   int have_links;
-  void *rlinks[3];       // per hr_prec: rows-kernel link layout (see hr_rows_nch), or null
+  void *rlinks[4];       // per hr_prec: rows-kernel link layout (see hr_rows_nch), or null
   int dom;               // 1: a time slab [t0, t0 + T) of a T_global lattice (faces via halo buffers)
   int t0, Tg;            // global time origin and extent (0 and T for a whole lattice)
   void *halo[4];         // single-process exchange buffers: send_up, send_down, recv_up, recv_down
@@ -160,7 +160,9 @@ struct HopArgs {
 // One launch shape of the hopping stencil: split_g = 0 is the one-site-per-
 // thread kernel with `bs` threads per block and register-budget variant
 // `regs` (0: compiler's choice for 256 threads, 1: up to ~170 registers,
-// 2: at most ~85 registers, 3: at most 128 registers); split_g = G > 0 is the colour-split kernel with
+// 2: at most ~85 registers, 3: at most 128 registers, 4: the budget of 1
+// with a one-wave grid whose blocks loop over the work items, FP32 only);
+// split_g = G > 0 is the colour-split kernel with
 // G threads per site (128 threads per block).
 // mrhs = S > 0 selects the multi-right-hand-side kernel (S sites per block,
 // links staged once per site for all right-hand sides of the block);
@@ -202,6 +204,10 @@ __host__ __device__ constexpr int hr_rows_dp(int d, int is_real) { return is_rea
 __host__ __device__ constexpr int hr_rows_nch(int d, int is_real) {
   return is_real ? d * hr_rows_dp(d, is_real) / 2 : d * d;
 }
+// The rows layout holds 16 matrices of hr_rows_nch chunk rows, then
+// HR_ROWS_SLACK zeroed chunk rows that the rows kernel's last column batch may
+// read past the last matrix.
+#define HR_ROWS_SLACK 16
 
 // The (d_R, rows per warp) pairs built for the rows kernel; one X(D, REAL, R)
 // line each.  Shared by the candidate list and every dispatch.

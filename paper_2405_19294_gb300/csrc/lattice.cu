@@ -184,8 +184,10 @@ extern "C" int hr_lattice_destroy(hr_lattice *lat) {
   if (!lat) return HR_ERR_ARG;
   cudaDeviceSynchronize();  // the solver streams too: nothing may still use what is freed below
   hr_bicgstab_forget(lat);
-  for (int p = 0; p < 3; ++p) hr_dev_free(lat->rlinks[p]);
-  for (int p = 0; p < 4; ++p) hr_dev_free(lat->links[p]);
+  for (int p = 0; p < 4; ++p) {
+    hr_dev_free(lat->links[p]);
+    hr_dev_free(lat->rlinks[p]);
+  }
   for (int b = 0; b < 4; ++b) hr_dev_free(lat->halo[b]);
   hr_dev_free(lat->clover_term);
   for (int p = 0; p < 3; ++p) {

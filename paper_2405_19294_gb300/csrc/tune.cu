@@ -24,13 +24,21 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
   const bool site_mrhs = is_real ? (d == 3 || d == 8) : (d >= 2 && d <= 6);
   if (prec == HR_FF) {
     // float-float: its site kernel (hop_ff.cuh), compiler's register choice
-    // or (d_R <= 3, where it does not spill) the high budget
-    if (!site) return 0;
-    const int bss[4] = {64, 128, 32, 256};
-    for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0, 0};
-    if (d <= 3) {
-      out[n++] = HopShape{0, 64, 1, 0};
-      out[n++] = HopShape{0, 128, 1, 0};
+    // or (d_R <= 3, where it does not spill) the high budget, and the rows
+    // kernel (no clover)
+    if (site) {
+      const int bss[4] = {64, 128, 32, 256};
+      for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0, 0};
+      if (d <= 3) {
+        out[n++] = HopShape{0, 64, 1, 0};
+        out[n++] = HopShape{0, 128, 1, 0};
+      }
+    }
+    if (!clover) {
+#define HR_ROWS_CAND(DD, RE, RR) \
+  if (d == DD && (is_real != 0) == RE) out[n++] = HopShape{0, 32 * ((DD + RR - 1) / RR), 0, 0, RR};
+      HR_ROWS_SHAPES(HR_ROWS_CAND)
+#undef HR_ROWS_CAND
     }
     return n;
   }
@@ -54,6 +62,10 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
       out[n++] = HopShape{0, 64, 2, 0};
       out[n++] = HopShape{0, 32, 3, 0};
       out[n++] = HopShape{0, 64, 3, 0};
+      if (prec == HR_F32) {  // one-wave grids
+        out[n++] = HopShape{0, 32, 4, 0};
+        out[n++] = HopShape{0, 64, 4, 0};
+      }
     }
   }
   if (!clover) {

@@ -115,9 +115,9 @@ def test_ff_links_follow_new_gauge_field(hr):
     assert rel_err(got, ref, Geometry(T, L).parity == 0) < TOL[0]
 
 
-@pytest.mark.parametrize("N,rep", [(3, "fund"), (2, "adj"), (6, "fund"), (3, "adj")])
+@pytest.mark.parametrize("N,rep", [(3, "fund"), (2, "adj"), (6, "fund"), (3, "adj"), (4, "sym"), (6, "adj")])
 def test_every_ff_shape(hr, N, rep):
-    T, L, m0 = 10, 6, -0.3
+    T, L, m0 = (10, 6, -0.3) if N < 4 or rep == "fund" else (4, 6, -0.3)
     lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
     psi = inputs.gaussian_spinor(6, T, L, lat.d)
     mask = Geometry(T, L).parity == 0
@@ -130,17 +130,29 @@ def test_every_ff_shape(hr, N, rep):
         assert rel_err(got, f64, mask) < FF_VS_F64, sh
 
 
-def test_ff_unsupported_class_reports(hr):
-    """d_R > 8 has no float-float kernel: hr_dphi says so rather than computing anything."""
-    lat, _ = gpu_lattice(hr, 4, 4, 4, "sym", 1.0, 0.0)  # d_R = 10
-    f, g = lat.new_field(0, FF), lat.new_field(0, FF)
-    with pytest.raises(hr.HrError) as e:
-        lat.dphi(g, f, 0, -0.3, 0.0, FF)
-    assert e.value.status == -7
+LARGE = [(4, "sym"), (6, "asym"), (4, "adj"), (6, "sym"), (5, "adj"), (6, "adj"), (9, "fund"), (12, "fund")]
+
+
+@pytest.mark.parametrize("N,rep", LARGE)
+def test_dphi_ff_parity_large_representations(hr, N, rep):
+    """d_R = 9 ... 35: the rows kernel in float-float (several blocks, ragged tail)."""
+    T, L, m0, eps = 4, 6, -0.3, 1.0
+    lat, _ = gpu_lattice(hr, T, L, N, rep, eps, 0.0)
+    op = oracle_operator(T, L, N, rep, eps, m0, 0.0)
+    psi = inputs.gaussian_spinor(1, T, L, lat.d)
+    g = op.geom
+    for parity in (0, 2):
+        for dagger in (0, 1):
+            got = _apply(lat, psi, parity, m0, 0.0, FF, dagger)[0]
+            ref = _oracle_apply(op, psi[0], parity, dagger)
+            mask = np.ones(g.V, bool) if parity == 2 else g.parity == parity
+            assert rel_err(got, ref, mask) < TOL[0], (parity, dagger)
+            f64 = _apply(lat, psi, parity, m0, 0.0, 0, dagger)[0]
+            assert rel_err(got, f64, mask) < FF_VS_F64, (parity, dagger, rel_err(got, f64, mask))
 
 
 @pytest.mark.parametrize("inner", [1, 2])
-@pytest.mark.parametrize("N,rep,csw", [(3, "fund", 0.0), (2, "adj", 0.0), (3, "sym", 1.0)])
+@pytest.mark.parametrize("N,rep,csw", [(3, "fund", 0.0), (2, "adj", 0.0), (3, "sym", 1.0), (4, "sym", 0.0)])
 def test_mixed_cg_ff_outer_oracle_residual(hr, inner, N, rep, csw):
     """The oracle's FP64 residual of the solution meets the target, the residual the
     library reports from its float-float arithmetic agrees with it, and the two outer
