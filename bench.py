@@ -811,9 +811,16 @@ def config4(hr, inputs, torch, nlat=64):
            for k, lt in enumerate(lats)]
     t_p = time.perf_counter() - t0
     rec["cg_1e-8"] = {"status": rc, "batched_s": round(t_b, 4), "per_lattice_s": round(t_p, 4),
-                      "speedup": round(t_p / t_b, 2),
+                      "speedup": round(t_p / t_b, 2), "outer_residuals": "ff",
                       "max_true_residual_batched": max(s_["true_residual"] for s_ in st),
                       "max_true_residual_per_lattice": max(r["true_residual"] for r in per)}
+    # the batched solve with FP64 outer residuals, for comparison
+    batch.cg_solve(xs, bs, 0, m0s, 1e-8, inner_prec=hr.F32, outer_prec=hr.F64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc64, st64 = batch.cg_solve(xs, bs, 0, m0s, 1e-8, inner_prec=hr.F32, outer_prec=hr.F64)
+    rec["cg_1e-8_fp64_outer"] = {"status": rc64, "batched_s": round(time.perf_counter() - t0, 4),
+                                 "max_true_residual_batched": max(s_["true_residual"] for s_ in st64)}
     batch.close()
     for lt in lats:
         lt.close()

@@ -99,9 +99,9 @@ typedef struct {
   double inner_tol;  /* relative residual reduction per inner solve (mixed only) */
   int nrhs;          /* number of right-hand sides stored back to back */
   int check_every;   /* inner iterations between residual checks on the host */
-  int outer_prec;    /* mixed hr_cg_solve / hr_bicgstab_solve: arithmetic of the outer
-                        residual, HR_F64 (0) or HR_FF (float-float; time slabs use
-                        FP64).  Ignored elsewhere */
+  int outer_prec;    /* mixed hr_cg_solve / hr_bicgstab_solve / hr_batch_cg_solve:
+                        arithmetic of the outer residual, HR_F64 (0) or HR_FF
+                        (float-float; time slabs use FP64).  Ignored elsewhere */
 } hr_cg_params;
 
 typedef struct {
@@ -338,8 +338,8 @@ int hr_batch_set_shape(hr_batch *batch, int d, int is_real, int prec, int shape)
  * (kernel-call overhead dominates small volumes, Sec. 3.1.1, Sec. 3.2):
  * out[i] = Dhat_p in[i] (or its adjoint) on lattice i, parity EVEN or ODD,
  * bare mass m0[i] (host array); internal single-parity fields of precision
- * prec, one rhs each.  The first call per precision times each class's
- * launch shapes (outside stream capture). */
+ * prec (HR_FF included), one rhs each.  The first call per precision times
+ * each class's launch shapes (outside stream capture). */
 int hr_batch_dphi(hr_batch *batch, void *const *out, const void *const *in, int parity, const double *m0,
                   int prec, int dagger);
 
@@ -349,7 +349,9 @@ int hr_batch_dphi(hr_batch *batch, void *const *out, const void *const *in, int 
  * x overwritten).  params->inner_prec HR_F32 or HR_F16: the inner CG of all
  * lattices runs in lock step as one CUDA graph per chunk of
  * params->check_every iterations; converged lattices are frozen on the device
- * and skipped; FP64 defect correction per lattice between chunks.
+ * and skipped; FP64 defect correction per lattice between chunks
+ * (params->outer_prec = HR_FF: the outer residuals in float-float, batched
+ * over the lattices as the FP64 ones are).
  * stats[i] (n entries) receives each lattice's iterations and residual.
  * Synchronous.  Errors as hr_cg_solve. */
 int hr_batch_cg_solve(hr_batch *batch, void *const *x, const void *const *b, int parity, const double *m0,

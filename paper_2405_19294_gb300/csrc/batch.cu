@@ -12,8 +12,9 @@
 // The whole inner iteration (4 x classes hop launches + 3 BLAS launches) is
 // captured once into a CUDA graph and replayed in chunks; a lattice whose CG
 // has converged sets its frozen flag and its tiles are skipped by the hop and
-// update kernels while the others continue.  The FP64 outer defect correction
-// (true residual, rescaling, x update) runs per lattice between chunks.
+// update kernels while the others continue.  The outer defect correction
+// (true residual, rescaling, x update) runs between chunks, batched over the
+// lattices, in FP64 or (outer_prec = HR_FF) in float-float.
 #include <algorithm>
 #include <chrono>
 #include <map>
@@ -35,11 +36,11 @@ struct BLat {         // per-lattice view for the batched vector kernels
 
 struct BClass {
   int d, is_real;
-  HopShape sh[3];        // launch shape per precision
+  HopShape sh[4];        // launch shape per precision (hr_prec, HR_FF included)
   std::vector<int> members;
-  int2 *items[3];        // device work list (lattice index, tile) per precision
-  int nitems[3];
-  int tuned[3];
+  int2 *items[4];        // device work list (lattice index, tile) per precision
+  int nitems[4];
+  int tuned[4];
 };
 
 struct BPair {          // per-lattice (x, y) of a batched y = a x + b y
@@ -51,7 +52,8 @@ struct BPair {          // per-lattice (x, y) of a batched y = a x + b y
 
 enum { B_RR0 = 0, B_RR1, B_PAP, B_ALPHA, B_BETA, B_STOP, B_A, B_B, B_OUT, B_NS };
 // batched axpby operand pairs of the outer loop
-enum { P_B_R = 0, P_AP_R, P_R_RL, P_RL_PL, P_XL_X, P_XL_XL, B_NPAIRS };
+// (P_B_BO, P_XO_X: b into and x out of the float-float outer iterate)
+enum { P_B_R = 0, P_AP_R, P_R_RL, P_RL_PL, P_XL_X, P_XL_XL, P_B_BO, P_XO_X, B_NPAIRS };
 
 int launch_multi(int prec, const BClass &c, const HopK *descs, const int *frozen, cudaStream_t s) {
   const HopShape sh = c.sh[prec];
@@ -59,6 +61,7 @@ int launch_multi(int prec, const BClass &c, const HopK *descs, const int *frozen
     case HR_F64: return hr_launch_hop_multi_f64(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
     case HR_F32: return hr_launch_hop_multi_f32(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
     case HR_F16: return hr_launch_hop_multi_f16(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
+    case HR_FF: return hr_launch_hop_multi_ff(c.d, c.is_real, sh, descs, c.items[prec], c.nitems[prec], frozen, s);
   }
   return HR_ERR_ARG;
 }
@@ -175,7 +178,7 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
       BClass c;
       c.d = lats[i]->d;
       c.is_real = lats[i]->is_real;
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < 4; ++q) {
         HopShape shapes[HR_MAX_SHAPES];
         if (hr_hop_shapes(c.d, c.is_real, q, 0, 0, shapes) < 1) {
           delete b;
@@ -194,7 +197,7 @@ extern "C" int hr_batch_create(int n, hr_lattice *const *lats, hr_batch **out) {
   }
   int rc = HR_OK;
   for (auto &c : b->cls)
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 4; ++q)
       if (rc == HR_OK) rc = build_items(c, b->lats, q);
   std::vector<int2> bitems;
   for (int i = 0; i < n; ++i) {
@@ -269,7 +272,7 @@ extern "C" int hr_batch_destroy(hr_batch *b) {
     if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   for (auto &c : b->cls)
-    for (int q = 0; q < 3; ++q) cudaFree(c.items[q]);
+    for (int q = 0; q < 4; ++q) cudaFree(c.items[q]);
   cudaFree(b->d_desc);
   cudaFreeHost(b->h_desc);
   cudaFree(b->d_pairs);
@@ -368,7 +371,7 @@ static int tune_classes(hr_batch *b, int prec, int slot0, cudaStream_t s) {
 // Pin the launch shape of the class (d, is_real) at precision prec instead of
 // timing its candidates; the shape must be one of them.
 extern "C" int hr_batch_set_shape(hr_batch *b, int d, int is_real, int prec, int shape) {
-  if (!b || prec < HR_F64 || prec > HR_F16) return HR_ERR_ARG;
+  if (!b || prec < HR_F64 || prec > HR_FF) return HR_ERR_ARG;
   for (auto &c : b->cls) {
     if (c.d != d || c.is_real != (is_real != 0)) continue;
     HopShape shapes[HR_MAX_SHAPES];
@@ -409,10 +412,12 @@ static int batch_dhat(hr_batch *b, int prec, int slot0, const int *frozen, cudaS
 
 extern "C" int hr_batch_dphi(hr_batch *b, void *const *out, const void *const *in, int parity, const double *m0,
                              int prec, int dagger) {
-  if (!b || !out || !in || !m0 || (parity != HR_EVEN && parity != HR_ODD) || prec < HR_F64 || prec > HR_F16)
+  if (!b || !out || !in || !m0 || (parity != HR_EVEN && parity != HR_ODD) || prec < HR_F64 || prec > HR_FF)
     return HR_ERR_ARG;
   for (int i = 0; i < b->n; ++i)
     if (!out[i] || !in[i] || out[i] == in[i]) return HR_ERR_ARG;
+  if (prec == HR_FF)
+    for (auto *lat : b->lats) HR_TRY(hr_ff_prepare(lat, 0, 0.0, b->stream));
   HR_TRY(fill_desc(b, 0, prec, out, in, parity, m0, dagger));
   HR_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(HopK) * 2 * b->n, cudaMemcpyHostToDevice, b->stream));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -520,35 +525,43 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   cudaGraphDestroy(graph);
   HR_CUDA(ce);
 
-  // ---------------------------------------------------------- FP64 outer loop
+  // -------------------------------------------------------------- outer loop
   // Every outer-loop vector operation is one batched launch over all lattices
-  // (per-lattice a, b and skip flags); the FP64 true residual uses the
-  // multi-lattice FP64 hop (descriptor stages 4..7).
-  std::vector<void *> t64(n), Ap64(n), r64(n);
+  // (per-lattice a, b and skip flags); the true residual uses the
+  // multi-lattice hop of precision po (descriptor stages 4..7): FP64, or
+  // float-float with the outer iterate xo and bo = b as float-float fields
+  // (the FP64 workspace's otherwise unused p and x buffers).
+  const int po = prm->outer_prec == HR_FF ? HR_FF : HR_F64;
+  std::vector<void *> t64(n), Ap64(n), r64(n), xo(n), bo(n);
   for (int i = 0; i < n; ++i) {
     t64[i] = hr_cg_field(b->lats[i], HR_F64, 3);
     Ap64[i] = hr_cg_field(b->lats[i], HR_F64, 2);
     r64[i] = hr_cg_field(b->lats[i], HR_F64, 0);
+    xo[i] = po == HR_FF ? hr_cg_field(b->lats[i], HR_F64, 4) : x[i];
+    bo[i] = po == HR_FF ? hr_cg_field(b->lats[i], HR_F64, 1) : const_cast<void *>(bsrc[i]);
+    if (po == HR_FF) HR_TRY(hr_ff_prepare(b->lats[i], 0, 0.0, s));
   }
-  HR_TRY(fill_desc(b, 4, HR_F64, t64.data(), (const void *const *)x, parity, m0, 0));        // t = Dhat x
-  HR_TRY(fill_desc(b, 6, HR_F64, Ap64.data(), (const void *const *)t64.data(), parity, m0, 1));  // Ap = Dhat^+ t
+  HR_TRY(fill_desc(b, 4, po, t64.data(), (const void *const *)xo.data(), parity, m0, 0));     // t = Dhat x
+  HR_TRY(fill_desc(b, 6, po, Ap64.data(), (const void *const *)t64.data(), parity, m0, 1));   // Ap = Dhat^+ t
   for (int i = 0; i < n; ++i) {
     hr_lattice *lat = b->lats[i];
     const int nblk = hr_blas_blocks(lat->Vh);
     auto pair = [&](int which, const void *px, void *py) {
       b->h_pairs[(size_t)which * n + i] = BPair{(const char *)px, (char *)py, lat->Vh, lat->d, nblk};
     };
-    pair(P_B_R, bsrc[i], r64[i]);
+    pair(P_B_R, bo[i], r64[i]);
     pair(P_AP_R, Ap64[i], r64[i]);
     pair(P_R_RL, r64[i], b->h_blat[i].r);
     pair(P_RL_PL, b->h_blat[i].r, pl[i]);
-    pair(P_XL_X, b->h_blat[i].x, x[i]);
+    pair(P_XL_X, b->h_blat[i].x, xo[i]);
     pair(P_XL_XL, b->h_blat[i].x, b->h_blat[i].x);
+    pair(P_B_BO, bsrc[i], bo[i]);
+    pair(P_XO_X, xo[i], x[i]);
   }
   HR_CUDA(cudaMemcpyAsync(b->d_desc + (size_t)4 * n, b->h_desc + (size_t)4 * n, sizeof(HopK) * 4 * n,
                           cudaMemcpyHostToDevice, s));
   HR_CUDA(cudaMemcpyAsync(b->d_pairs, b->h_pairs, sizeof(BPair) * B_NPAIRS * n, cudaMemcpyHostToDevice, s));
-  HR_TRY(tune_classes(b, HR_F64, 4, s));
+  HR_TRY(tune_classes(b, po, 4, s));
   int *skip = b->frozen;  // reused between phases: 1 = lattice done (outer) / frozen (inner)
   std::vector<double> bn2(n), rn2(n);
   std::vector<int> active(n, 1), skipv(n);
@@ -575,6 +588,11 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
     else if (px == 1 && py == 0) BAX(1, 0);
     else if (px == 1 && py == 1) BAX(1, 1);
     else if (px == 1 && py == 2) BAX(1, 2);
+    else if (px == 0 && py == 3) BAX(0, 3);
+    else if (px == 3 && py == 3) BAX(3, 3);
+    else if (px == 3 && py == 1) BAX(3, 1);
+    else if (px == 1 && py == 3) BAX(1, 3);
+    else if (px == 3 && py == 0) BAX(3, 0);
     else return HR_ERR_UNSUPPORTED;
 #undef BAX
     return hr_check_launch("baxpby_kernel");
@@ -588,12 +606,16 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   };
   std::vector<double> one(n, 1.0), zero(n, 0.0), mone(n, -1.0), va(n);
   // x = 0; r = b; |b|^2
-  for (int i = 0; i < n; ++i)
-    HR_CUDA(cudaMemsetAsync(x[i], 0, hr_spinor_field_bytes(b->lats[i]->Vh, b->lats[i]->d, HR_F64), s));
+  for (int i = 0; i < n; ++i) {
+    const size_t fb = hr_spinor_field_bytes(b->lats[i]->Vh, b->lats[i]->d, HR_F64);
+    HR_CUDA(cudaMemsetAsync(x[i], 0, fb, s));
+    if (po == HR_FF) HR_CUDA(cudaMemsetAsync(xo[i], 0, fb, s));
+  }
   HR_TRY(set_skip());
   HR_TRY(set(B_A, one));
   HR_TRY(set(B_B, zero));
-  HR_TRY(axpby(P_B_R, HR_F64, HR_F64, 1));
+  if (po == HR_FF) HR_TRY(axpby(P_B_BO, HR_F64, HR_FF, 0));
+  HR_TRY(axpby(P_B_R, po, po, 1));
   HR_TRY(fetch_norms(bn2));
   for (int i = 0; i < n; ++i) rn2[i] = bn2[i];
 
@@ -625,7 +647,7 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
     HR_TRY(set_skip());
     HR_TRY(set(B_A, va));
     HR_TRY(set(B_B, zero));
-    HR_TRY(axpby(P_R_RL, HR_F64, HR_F32, 0));
+    HR_TRY(axpby(P_R_RL, po, HR_F32, 0));
     HR_TRY(set(B_A, one));
     HR_TRY(axpby(P_RL_PL, HR_F32, lo, 0));
     HR_TRY(set(B_A, zero));
@@ -654,21 +676,28 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
       status = HR_ERR_BREAKDOWN;
       break;
     }
-    // x += |r| xl (active lattices), then r = b - M x in FP64
+    // x += |r| xl (active lattices), then r = b - M x (precision po)
     HR_TRY(set_skip());
     for (int i = 0; i < n; ++i) va[i] = sqrt(rn2[i]);
     HR_TRY(set(B_A, va));
     HR_TRY(set(B_B, one));
-    HR_TRY(axpby(P_XL_X, HR_F32, HR_F64, 0));
-    HR_TRY(batch_dhat(b, HR_F64, 4, skip, s));
-    HR_TRY(batch_dhat(b, HR_F64, 6, skip, s));
+    HR_TRY(axpby(P_XL_X, HR_F32, po, 0));
+    HR_TRY(batch_dhat(b, po, 4, skip, s));
+    HR_TRY(batch_dhat(b, po, 6, skip, s));
     HR_TRY(set(B_A, one));
     HR_TRY(set(B_B, zero));
-    HR_TRY(axpby(P_B_R, HR_F64, HR_F64, 0));
+    HR_TRY(axpby(P_B_R, po, po, 0));
     HR_TRY(set(B_A, mone));
     HR_TRY(set(B_B, one));
-    HR_TRY(axpby(P_AP_R, HR_F64, HR_F64, 1));
+    HR_TRY(axpby(P_AP_R, po, po, 1));
     HR_TRY(fetch_norms(rn2));
+  }
+  if (po == HR_FF) {  // x = the FP64 value of every lattice's float-float iterate
+    std::fill(active.begin(), active.end(), 1);
+    HR_TRY(set_skip());
+    HR_TRY(set(B_A, one));
+    HR_TRY(set(B_B, zero));
+    HR_TRY(axpby(P_XO_X, HR_FF, HR_F64, 0));
   }
   cudaGraphExecDestroy(exec);
   HR_CUDA(cudaStreamSynchronize(s));

@@ -58,9 +58,42 @@ int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st) {
   return HR_OK;
 }
 
-#define HR_FF_CLASS(DD, RE, NAME) void NAME(const HopK &, SkipK, dim3, int, int, cudaStream_t, int);
+#define HR_FF_CLASS(DD, RE, NAME)                                   \
+  void NAME(const HopK &, SkipK, dim3, int, int, cudaStream_t, int); \
+  const void *NAME##_multi();
 HR_FF_CLASSES(HR_FF_CLASS)
 #undef HR_FF_CLASS
+const void *hr_ff_rows_multi(int d, int is_real, int rows, int *block, size_t *smem);
+
+// Persistent multi-lattice launch (grid = min(work items, SMs x resident
+// blocks)): the site kernel of the class, or the rows kernel.
+int hr_launch_hop_multi_ff(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                           const int *frozen, cudaStream_t s) {
+  int block = sh.bs;
+  size_t smem = 0;
+  const void *fn = nullptr;
+  if (sh.rows) {
+    fn = hr_ff_rows_multi(d, is_real, sh.rows, &block, &smem);
+  } else if (!sh.split_g && !sh.mrhs) {
+    const bool real = is_real != 0;
+#define HR_FF_CLASS(DD, RE, NAME) \
+  if (d == DD && real == RE) fn = NAME##_multi();
+    HR_FF_CLASSES(HR_FF_CLASS)
+#undef HR_FF_CLASS
+  }
+  if (!fn) return HR_ERR_UNSUPPORTED;
+  if (nitems <= 0) return HR_OK;
+  int dev = 0, sms = 0, per_sm = 0;
+  HR_CUDA(cudaGetDevice(&dev));
+  HR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > nitems) grid = nitems;
+  void *args[] = {(void *)&descs, (void *)&items, (void *)&nitems, (void *)&frozen};
+  HR_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  return HR_OK;
+}
 
 int hr_launch_hop_ff_rows(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int rows);
 

@@ -190,6 +190,21 @@ __global__ void __launch_bounds__(MAXT, MINB) hop_ff_kernel(HopK k, SkipK sk) {
   if (i < k.Vh) hop_site_ff<D, REAL>(k, i, rhs);
 }
 
+// Persistent multi-lattice form (the batched solver's outer residuals): every
+// block walks the work list of (lattice, tile) items with stride gridDim.x, as
+// hop_multi_kernel does for the other precisions.
+template <int D, bool REAL>
+__global__ void __launch_bounds__(256, 1) hop_ff_multi_kernel(const HopK *descs, const int2 *items, int nitems,
+                                                              const int *frozen) {
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int2 it = items[w];
+    if (frozen && frozen[it.x]) continue;
+    const HopK k = descs[it.x];
+    const int64_t i = (int64_t)it.y * blockDim.x + threadIdx.x;
+    if (i < k.Vh) hop_site_ff<D, REAL>(k, i, 0);
+  }
+}
+
 // (d_R, real links, launcher name) of every class built in float-float
 #define HR_FF_CLASSES(X)                                                                               \
   X(2, false, hr_ff_c2) X(3, false, hr_ff_c3) X(3, true, hr_ff_r3) X(4, false, hr_ff_c4)             \
@@ -209,7 +224,10 @@ static void launch_site_ff(const HopK &k, SkipK sk, dim3 grid, int bs, int varia
   launch_pdl(hop_ff_kernel<D, REAL, 256, 1>, k, sk, grid, bs, st, pdl);
 }
 
+// NAME launches the class's site kernel; NAME##_multi returns its
+// multi-lattice kernel
 #define HR_FF_DEFINE(DD, RE, NAME)                                                                   \
   void NAME(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {   \
     launch_site_ff<DD, RE>(k, sk, grid, bs, variant, st, pdl);                                       \
-  }
+  }                                                                                                  \
+  const void *NAME##_multi() { return (const void *)hop_ff_multi_kernel<DD, RE>; }

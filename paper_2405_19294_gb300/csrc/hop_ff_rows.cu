@@ -5,3 +5,8 @@
 int hr_launch_hop_ff_rows(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, int rows) {
   return rows_dispatch<3>(lat, a, s, rows);
 }
+
+// the multi-lattice rows kernel (batched solver) and its block and shared memory
+const void *hr_ff_rows_multi(int d, int is_real, int rows, int *block, size_t *smem) {
+  return rows_multi_ptr<3>(d, is_real, rows, block, smem);
+}

@@ -260,6 +260,8 @@ int hr_launch_hop_multi_f32(int d, int is_real, HopShape sh, const HopK *descs, 
                             const int *frozen, cudaStream_t s);
 int hr_launch_hop_multi_f16(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
                             const int *frozen, cudaStream_t s);
+int hr_launch_hop_multi_ff(int d, int is_real, HopShape sh, const HopK *descs, const int2 *items, int nitems,
+                           const int *frozen, cudaStream_t s);
 
 // cg.cu: per-lattice solver workspace (5 fields per precision: r, p, Ap, t, x)
 int hr_cg_workspace(hr_lattice *lat, int prec, size_t bytes);

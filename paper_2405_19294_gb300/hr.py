@@ -372,9 +372,11 @@ class Batch:
                "hr_batch_dphi")
 
     def cg_solve(self, xs, bs, parity: int, m0s, tol: float, inner_prec: int = F32, inner_tol: float = 0.0,
-                 maxit: int = 100000, check_every: int = 10, raise_on_error: bool = True):
+                 maxit: int = 100000, check_every: int = 10, raise_on_error: bool = True, outer_prec: int = FF):
+        """Lock-step mixed CG on every lattice of the batch; outer residuals in outer_prec
+        (FF: float-float, F64) (hr_batch_cg_solve)."""
         m = (C.c_double * len(m0s))(*m0s)
-        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, 1, check_every)
+        prm = hr_cg_params(tol, maxit, inner_prec, inner_tol, 1, check_every, outer_prec)
         st = (hr_cg_stats * len(xs))()
         rc = _lib.hr_batch_cg_solve(self._h, self._ptrs(xs), self._ptrs(bs), parity, m, C.byref(prm), st)
         if rc != 0 and raise_on_error:
