@@ -96,7 +96,8 @@ typedef struct {
   double tol;        /* target true relative residual |b - M x| / |b| (FP64) */
   int maxit;         /* cap on inner iterations (all outer steps together) */
   int inner_prec;    /* hr_prec of the inner solver; HR_F64 = plain FP64 CG */
-  double inner_tol;  /* relative residual reduction per inner solve (mixed only) */
+  double inner_tol;  /* relative residual reduction per inner solve (mixed only; 0: 1e-5 for
+                        HR_F32, 3e-3 for HR_F16) */
   int nrhs;          /* number of right-hand sides stored back to back */
   int check_every;   /* inner iterations between residual checks on the host */
   int outer_prec;    /* mixed hr_cg_solve / hr_bicgstab_solve / hr_batch_cg_solve:

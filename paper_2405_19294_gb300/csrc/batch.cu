@@ -437,7 +437,7 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   const int n = b->n, lo = prm->inner_prec;
   const int check_every = std::max(2, (prm->check_every > 0 ? prm->check_every : 10) & ~1);
   const int maxit = prm->maxit > 0 ? prm->maxit : 100000;
-  const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 1e-2);
+  const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 3e-3);
   cudaStream_t s = b->s;
   // order after the caller's stream
   HrEvent ev_owner;

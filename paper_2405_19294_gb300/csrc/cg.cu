@@ -415,7 +415,7 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
     flo.fb = fblo;
     void *xl = w->f[HR_F32][4], *rl = w->f[HR_F32][0];
     void *pl = w->f[lo][1], *Apl = w->f[lo][2], *tl = w->f[lo][3];
-    const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 1e-2);
+    const double inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (lo == HR_F32 ? 1e-5 : 3e-3);
     const int maxouter = 200;
     while (true) {
       bool ok = true;
