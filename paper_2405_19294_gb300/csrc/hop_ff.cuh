@@ -26,6 +26,29 @@ __device__ __forceinline__ cx<ff> ff_rot(cx<ff> b, float f, bool odd) {
   return mk(mkff(f * bx.h, f * bx.l), mkff(f * by.h, f * by.l));
 }
 
+// acc = B acc for the two packed Hermitian chiral blocks of the clover field
+// at site i (A or A^{-1}), one block at a time in a loop (one copy of the
+// block product's code)
+template <int D>
+__device__ __forceinline__ void ff_clover_inplace(const void *cl, int64_t Vh, int64_t i, cx<ff> (&acc)[D][4]) {
+#pragma unroll 1
+  for (int b = 0; b < 2; ++b) {
+    cx<ff> v[2 * D], w[2 * D];
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[s2 * D + c] = b ? acc[c][2 + s2] : acc[c][s2];
+    herm_apply<D, 3>(cl, Vh, i, b * 2 * D * D, v, w);
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (b) acc[c][2 + s2] = w[s2 * D + c];
+        else acc[c][s2] = w[s2 * D + c];
+      }
+  }
+}
+
 template <int D, bool REAL>
 __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
   const size_t roff = (size_t)rhs * k.stride;
@@ -38,11 +61,27 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
   const int64_t slab = (int64_t)k.nch * Vh;
   const int64_t LLh = (int64_t)L * Lh;
 
+  // the self term of the second launch first, divided by coef (a power of two
+  // in every Schur and full-operator launch, so exactly): the hops then add
+  // into it and the epilogue's scaling by coef gives A self + coef H with no
+  // second D x 4 array live (which made the d_R = 6 clover kernel spill)
   cx<ff> acc[D][4];
+  if (k.mode == HOP_SELF) {
+    const char *self = reinterpret_cast<const char *>(k.self) + roff;
 #pragma unroll
-  for (int c = 0; c < D; ++c)
+    for (int c = 0; c < D; ++c) ld_colour<3>(self, Vh, i, c, acc[c]);
+    if (k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
+    const ff f(k.clover ? 1.0 / k.coef : k.diag / k.coef);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[c][q] = mk(ff(0), ff(0));
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[c][q] = scale(f, acc[c][q]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[c][q] = mk(ff(0), ff(0));
+  }
 
 #pragma unroll 1
   for (int n = 0; n < 8; ++n) {
@@ -121,60 +160,14 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
     }
   }
 
-  // ---- epilogue (hop.cuh's, in float-float) ----
+  // ---- epilogue: out = coef H (+ the self term folded in above), then
+  // A^{-1} in place for the first launch of a Schur Dhat with clover ----
   const ff coef(k.coef);
 #pragma unroll
   for (int c = 0; c < D; ++c)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[c][q] = scale(coef, acc[c][q]);
-  const bool scaled = k.mode == HOP_SCALED;
-  cx<ff> sv[D][4];
-  if (!scaled) {
-    const char *self = reinterpret_cast<const char *>(k.self) + roff;
-#pragma unroll
-    for (int c = 0; c < D; ++c) ld_colour<3>(self, Vh, i, c, sv[c]);
-  }
-  if (k.clover) {
-    // one copy of the block products for both modes: A^{-1} acc (scaled) or
-    // A self (self), each chiral block in turn (loops kept, as above, so that
-    // the code fits the instruction caches)
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (!scaled) {
-          const cx<ff> t = acc[c][q];
-          acc[c][q] = sv[c][q];
-          sv[c][q] = t;
-        }
-#pragma unroll 1
-    for (int b = 0; b < 2; ++b) {
-      cx<ff> v[2 * D], w[2 * D];
-#pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-        for (int c = 0; c < D; ++c) v[s2 * D + c] = b ? acc[c][2 + s2] : acc[c][s2];
-      herm_apply<D, 3>(k.clover, Vh, i, b * 2 * D * D, v, w);
-#pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          if (b) acc[c][2 + s2] = w[s2 * D + c];
-          else acc[c][s2] = w[s2 * D + c];
-        }
-    }
-    if (!scaled)
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[c][q] = acc[c][q] + sv[c][q];
-  } else if (!scaled) {
-    const ff dg(k.diag);
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[c][q] = axpy_r(dg, sv[c][q], acc[c][q]);
-  }
+  if (k.mode == HOP_SCALED && k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
 #pragma unroll
   for (int c = 0; c < D; ++c) st_colour_ff(out, Vh, i, c, acc[c]);
 }
