@@ -531,7 +531,9 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
   // multi-lattice hop of precision po (descriptor stages 4..7): FP64, or
   // float-float with the outer iterate xo and bo = b as float-float fields
   // (the FP64 workspace's otherwise unused p and x buffers).
-  const int po = prm->outer_prec == HR_FF ? HR_FF : HR_F64;
+  int use_ff = prm->outer_prec == HR_FF;
+  for (int i = 0; i < n && use_ff; ++i) HR_TRY(hr_ff_outer_usable(b->lats[i], 0, m0[i], 1, s, &use_ff));
+  const int po = use_ff ? HR_FF : HR_F64;
   std::vector<void *> t64(n), Ap64(n), r64(n), xo(n), bo(n);
   for (int i = 0; i < n; ++i) {
     t64[i] = hr_cg_field(b->lats[i], HR_F64, 3);
@@ -539,7 +541,6 @@ extern "C" int hr_batch_cg_solve(hr_batch *b, void *const *x, const void *const 
     r64[i] = hr_cg_field(b->lats[i], HR_F64, 0);
     xo[i] = po == HR_FF ? hr_cg_field(b->lats[i], HR_F64, 4) : x[i];
     bo[i] = po == HR_FF ? hr_cg_field(b->lats[i], HR_F64, 1) : const_cast<void *>(bsrc[i]);
-    if (po == HR_FF) HR_TRY(hr_ff_prepare(b->lats[i], 0, 0.0, s));
   }
   HR_TRY(fill_desc(b, 4, po, t64.data(), (const void *const *)xo.data(), parity, m0, 0));     // t = Dhat x
   HR_TRY(fill_desc(b, 6, po, Ap64.data(), (const void *const *)t64.data(), parity, m0, 1));   // Ap = Dhat^+ t

@@ -544,11 +544,9 @@ extern "C" int hr_bicgstab_solve(hr_lattice *lat, void *x, const void *b, int pa
   // outer residuals in float-float where that operator is built (mixed solves):
   // the iterate and b then live in the FP64 workspace's x and r buffers, which
   // the mixed solve does not otherwise use
-  HopShape ffs[HR_MAX_SHAPES];
-  const int po = (lo != HR_F64 && prm->outer_prec == HR_FF && !lat->dom &&
-                  hr_hop_shapes(lat->d, lat->is_real, HR_FF, csw != 0.0, nrhs > 1, ffs) > 0)
-                     ? HR_FF
-                     : HR_F64;
+  int use_ff = 0;
+  if (lo != HR_F64 && prm->outer_prec == HR_FF) HR_TRY(hr_ff_outer_usable(lat, csw != 0.0, m0, nrhs, s, &use_ff));
+  const int po = use_ff ? HR_FF : HR_F64;
   void *xo = po == HR_FF ? g_bi->f[HR_F64][0] : x;
   const void *bo = po == HR_FF ? g_bi->f[HR_F64][1] : b;
   HR_CUDA(cudaMemsetAsync(x, 0, bytes64, s));

@@ -347,11 +347,9 @@ extern "C" int hr_cg_solve(hr_lattice *lat, void *x, const void *b, int parity, 
   double bn2[HR_MAX_RHS], rn2[HR_MAX_RHS], v[HR_MAX_RHS];
   int status = HR_OK, iters = 0, outer = 0;
   // outer residuals in float-float where that operator is built (mixed solves only)
-  HopShape ffs[HR_MAX_SHAPES];
-  const int po = (lo != HR_F64 && prm->outer_prec == HR_FF && !lat->dom &&
-                  hr_hop_shapes(lat->d, lat->is_real, HR_FF, csw != 0.0, nrhs > 1, ffs) > 0)
-                     ? HR_FF
-                     : HR_F64;
+  int use_ff = 0;
+  if (lo != HR_F64 && prm->outer_prec == HR_FF) HR_TRY(hr_ff_outer_usable(lat, csw != 0.0, m0, nrhs, c.s, &use_ff));
+  const int po = use_ff ? HR_FF : HR_F64;
   // the outer iterate and b in precision po: x and b themselves for FP64, else
   // the FP64 workspace's spare x and p buffers (p is unused by the mixed solve)
   void *xo = po == HR_FF ? w->f[HR_F64][4] : x;

@@ -58,6 +58,20 @@ int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st) {
   return HR_OK;
 }
 
+int hr_ff_outer_usable(hr_lattice *lat, int clover, double m0, int nrhs, cudaStream_t st, int *use) {
+  *use = 0;
+  HopShape sh[HR_MAX_SHAPES];
+  if (lat->dom || hr_hop_shapes(lat->d, lat->is_real, HR_FF, clover, nrhs > 1, sh) < 1) return HR_OK;
+  const int rc = hr_ff_prepare(lat, clover, m0, st);
+  if (rc == HR_ERR_NOMEM) {  // no room for the float-float copies: the solver keeps FP64
+    cudaGetLastError();
+    return HR_OK;
+  }
+  HR_TRY(rc);
+  *use = 1;
+  return HR_OK;
+}
+
 #define HR_FF_CLASS(DD, RE, NAME)                                   \
   void NAME(const HopK &, SkipK, dim3, int, int, cudaStream_t, int); \
   const void *NAME##_multi();

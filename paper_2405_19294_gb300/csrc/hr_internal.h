@@ -245,6 +245,11 @@ int hr_launch_hop_ff(const hr_lattice *lat, const HopArgs &a, cudaStream_t s, Ho
 // clover blocks at m0) of a lattice, made on stream st when missing or stale
 int hr_f64_to_ff(void *out, const void *in, size_t nreal, cudaStream_t s);
 int hr_ff_prepare(hr_lattice *lat, int clover, double m0, cudaStream_t st);
+// *use = 1 when a mixed solve's outer residuals on lat can run in float-float:
+// a kernel exists for the class (whole lattices only) and the float-float
+// links and clover blocks are in place on st (made here if needed); 0 when
+// not, including when the device has no room for them (FP64 is used then)
+int hr_ff_outer_usable(hr_lattice *lat, int clover, double m0, int nrhs, cudaStream_t st, int *use);
 // tensor-core multi-rhs kernel (complex d_R = 3 ... 6), FP32 (FP16 pairs) / FP16
 int hr_launch_hop_tc_f32(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
 int hr_launch_hop_tc_f16(const hr_lattice *lat, const HopArgs &a, cudaStream_t s);
