@@ -150,7 +150,6 @@ struct HopArgs {
   double diag;            // multiplies self when no clover
   size_t field_stride;    // bytes between rhs fields (in, out, self)
   int nrhs;
-  double *norm_partials;  // optional fused |out|^2 per block (null = off)
   int tmask;              // 1: skip the t hops that cross the slab faces (sub-domain bulk pass)
   const double *skip_rr;  // with skip_stop: a rhs whose skip_rr <= skip_stop is done, its blocks
   const double *skip_stop;  // return at once (CG chunks past convergence); null = never skip
