@@ -182,3 +182,31 @@ def test_mixed_cg_ff_outer_oracle_residual(hr, inner, N, rep, csw):
         assert abs(st["true_residual"] - worst) <= 0.05 * worst, (outer, worst, st)
     for k in range(nr):
         assert rel_err(xs[FF][k], xs[0][k], ev) < 1e-8
+
+
+def test_ff_outer_falls_back_to_fp64_without_room(hr):
+    """When the float-float link copies cannot be allocated (an allocator that refuses every
+    request stands in for a full device), the mixed solve keeps FP64 outer residuals: it
+    converges, and its residual is bit for bit the FP64-outer solve's (the reductions are
+    deterministic)."""
+    import ctypes as C
+    T, L, N, rep, m0 = 8, 4, 3, "fund", -0.35
+    lat, _ = gpu_lattice(hr, T, L, N, rep, 1.0, 0.0)
+    ev = Geometry(T, L).parity == 0
+    b = np.where(ev[None, :, None, None], inputs.gaussian_spinor(24, T, L, lat.d), 0)
+    fb, fx = lat.new_field(0, 0), lat.new_field(0, 0)
+    lat.pack(fb, from_complex(b), 0, 0)
+    st64 = lat.cg_solve(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=1, outer_prec=0)  # workspaces in place
+    refuse = hr._ALLOC_FN(lambda nbytes, ctx: None)
+    keep = hr._FREE_FN(lambda ptr, nbytes, ctx: None)
+    assert hr._lib.hr_set_allocator(C.cast(refuse, C.c_void_p), C.cast(keep, C.c_void_p), None) == 0
+    try:
+        st = lat.cg_solve(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=1, outer_prec=FF)
+    finally:
+        assert hr._lib.hr_set_allocator(None, None, None) == 0
+    assert st["status"] == 0 and st["true_residual"] <= 1e-10
+    assert st["true_residual"] == st64["true_residual"]
+    # with room again, the same call runs in float-float (a different rounding of the same residual)
+    st_ff = lat.cg_solve(fx, fb, 0, m0, 0.0, 1e-10, inner_prec=1, outer_prec=FF)
+    assert st_ff["status"] == 0 and st_ff["true_residual"] <= 1e-10
+    assert st_ff["true_residual"] != st64["true_residual"]
