@@ -74,7 +74,8 @@ int hr_ff_outer_usable(hr_lattice *lat, int clover, double m0, int nrhs, cudaStr
 
 #define HR_FF_CLASS(DD, RE, NAME)                                   \
   void NAME(const HopK &, SkipK, dim3, int, int, cudaStream_t, int); \
-  const void *NAME##_multi();
+  const void *NAME##_multi();                                        \
+  size_t NAME##_smem(int bs);
 HR_FF_CLASSES(HR_FF_CLASS)
 #undef HR_FF_CLASS
 const void *hr_ff_rows_multi(int d, int is_real, int rows, int *block, size_t *smem);
@@ -91,7 +92,10 @@ int hr_launch_hop_multi_ff(int d, int is_real, HopShape sh, const HopK *descs, c
   } else if (!sh.split_g && !sh.mrhs) {
     const bool real = is_real != 0;
 #define HR_FF_CLASS(DD, RE, NAME) \
-  if (d == DD && real == RE) fn = NAME##_multi();
+  if (d == DD && real == RE) {    \
+    fn = NAME##_multi();          \
+    smem = NAME##_smem(block);    \
+  }
     HR_FF_CLASSES(HR_FF_CLASS)
 #undef HR_FF_CLASS
   }

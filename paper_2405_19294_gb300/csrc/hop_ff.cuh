@@ -26,31 +26,63 @@ __device__ __forceinline__ cx<ff> ff_rot(cx<ff> b, float f, bool odd) {
   return mk(mkff(f * bx.h, f * bx.l), mkff(f * by.h, f * by.l));
 }
 
+// The D x 4 complex float-float accumulator of one site: in registers, or
+// (SMEM, complex d_R >= 5) in shared memory at [a * 4 + q][thread], so that
+// the loop over the output rows a can stay rolled as well.  Unrolled over the
+// rows, the d_R = 6 stencil with its clover epilogue again outgrew the
+// instruction caches (stalled about 3 cycles per issued instruction waiting
+// for instructions, 31 % issue).
+template <int D, bool SMEM>
+struct FfAcc;
+template <int D>
+struct FfAcc<D, false> {
+  cx<ff> v[D][4];
+  __device__ __forceinline__ cx<ff> &operator()(int a, int q) { return v[a][q]; }
+};
+template <int D>
+struct FfAcc<D, true> {
+  cx<ff> *base;  // this thread's element (0, 0); element (a, q) is stride * (4 a + q) further
+  int stride;
+  __device__ __forceinline__ cx<ff> &operator()(int a, int q) { return base[(a * 4 + q) * stride]; }
+};
+// complex d_R >= 5 keeps its accumulator in shared memory
+template <int D, bool REAL>
+__host__ __device__ constexpr bool ff_smem_acc() {
+  return !REAL && D >= 5;
+}
+// dynamic shared memory of a block of bs threads
+template <int D, bool REAL>
+__host__ __device__ constexpr size_t ff_smem_bytes(int bs) {
+  return ff_smem_acc<D, REAL>() ? (size_t)bs * D * 4 * sizeof(cx<ff>) : 0;
+}
+
 // acc = B acc for the two packed Hermitian chiral blocks of the clover field
 // at site i (A or A^{-1}), one block at a time in a loop (one copy of the
 // block product's code)
-template <int D>
-__device__ __forceinline__ void ff_clover_inplace(const void *cl, int64_t Vh, int64_t i, cx<ff> (&acc)[D][4]) {
+template <int D, typename AccT>
+__device__ __forceinline__ void ff_clover_inplace(const void *cl, int64_t Vh, int64_t i, AccT &acc) {
 #pragma unroll 1
   for (int b = 0; b < 2; ++b) {
     cx<ff> v[2 * D], w[2 * D];
 #pragma unroll
     for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-      for (int c = 0; c < D; ++c) v[s2 * D + c] = b ? acc[c][2 + s2] : acc[c][s2];
+      for (int c = 0; c < D; ++c) v[s2 * D + c] = b ? acc(c, 2 + s2) : acc(c, s2);
     herm_apply<D, 3>(cl, Vh, i, b * 2 * D * D, v, w);
 #pragma unroll
     for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        if (b) acc[c][2 + s2] = w[s2 * D + c];
-        else acc[c][s2] = w[s2 * D + c];
+        if (b) acc(c, 2 + s2) = w[s2 * D + c];
+        else acc(c, s2) = w[s2 * D + c];
       }
   }
 }
 
+// smem: the block's dynamic shared memory (used when ff_smem_acc<D, REAL>())
 template <int D, bool REAL>
-__device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
+__device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs, unsigned char *smem) {
+  constexpr bool SM = ff_smem_acc<D, REAL>();
   const size_t roff = (size_t)rhs * k.stride;
   const char *in = reinterpret_cast<const char *>(k.in) + roff;
   char *out = reinterpret_cast<char *>(k.out) + roff;
@@ -61,26 +93,35 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
   const int64_t slab = (int64_t)k.nch * Vh;
   const int64_t LLh = (int64_t)L * Lh;
 
+  FfAcc<D, SM> acc;
+  if constexpr (SM) {
+    acc.base = reinterpret_cast<cx<ff> *>(smem) + threadIdx.x;
+    acc.stride = (int)blockDim.x;
+  }
   // the self term of the second launch first, divided by coef (a power of two
   // in every Schur and full-operator launch, so exactly): the hops then add
   // into it and the epilogue's scaling by coef gives A self + coef H with no
   // second D x 4 array live (which made the d_R = 6 clover kernel spill)
-  cx<ff> acc[D][4];
   if (k.mode == HOP_SELF) {
     const char *self = reinterpret_cast<const char *>(k.self) + roff;
 #pragma unroll
-    for (int c = 0; c < D; ++c) ld_colour<3>(self, Vh, i, c, acc[c]);
+    for (int c = 0; c < D; ++c) {
+      cx<ff> v4[4];
+      ld_colour<3>(self, Vh, i, c, v4);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc(c, q) = v4[q];
+    }
     if (k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
     const ff f(k.clover ? 1.0 / k.coef : k.diag / k.coef);
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[c][q] = scale(f, acc[c][q]);
+      for (int q = 0; q < 4; ++q) acc(c, q) = scale(f, acc(c, q));
   } else {
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[c][q] = mk(ff(0), ff(0));
+      for (int q = 0; q < 4; ++q) acc(c, q) = mk(ff(0), ff(0));
   }
 
 #pragma unroll 1
@@ -111,6 +152,14 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
       h0[c] = psi[0] + ff_rot(pa, -sig, odd);
       h1[c] = psi[1] + ff_rot(pb, f1, odd);
     }
+    // row a of the link product, added to the accumulator as its 4 spins
+    auto rebuild = [&](int a, const cx<ff> &r0, const cx<ff> &r1) {
+      const cx<ff> rm = tz ? r0 : r1, rn = tz ? r1 : r0;
+      acc(a, 0) = acc(a, 0) + r0;
+      acc(a, 1) = acc(a, 1) + r1;
+      acc(a, 2) = acc(a, 2) + ff_rot(rm, g2, odd);
+      acc(a, 3) = acc(a, 3) + ff_rot(rn, g3, odd);
+    };
     if constexpr (REAL) {
       // real links: chunk e >> 1, half e & 1 of entry e = a D + c (U^T backward)
       constexpr int NC = (D * D + 1) / 2;
@@ -129,16 +178,11 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
           r0 = rfma(ue, h0[c], r0);
           r1 = rfma(ue, h1[c], r1);
         }
-        const cx<ff> rm = tz ? r0 : r1, rn = tz ? r1 : r0;
-        acc[a][0] = acc[a][0] + r0;
-        acc[a][1] = acc[a][1] + r1;
-        acc[a][2] = acc[a][2] + ff_rot(rm, g2, odd);
-        acc[a][3] = acc[a][3] + ff_rot(rn, g3, odd);
+        rebuild(a, r0, r1);
       }
     } else {
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        // row a of U, or column a of U conjugated (U^+), loaded before the products
+      // row a of U, or column a of U conjugated (U^+), loaded before the products
+      auto row = [&](int a) {
         cx<ff> ur[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -151,11 +195,14 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
           r0 = cfma(ur[c], h0[c], r0);
           r1 = cfma(ur[c], h1[c], r1);
         }
-        const cx<ff> rm = tz ? r0 : r1, rn = tz ? r1 : r0;
-        acc[a][0] = acc[a][0] + r0;
-        acc[a][1] = acc[a][1] + r1;
-        acc[a][2] = acc[a][2] + ff_rot(rm, g2, odd);
-        acc[a][3] = acc[a][3] + ff_rot(rn, g3, odd);
+        rebuild(a, r0, r1);
+      };
+      if constexpr (SM) {
+#pragma unroll 1
+        for (int a = 0; a < D; ++a) row(a);
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) row(a);
       }
     }
   }
@@ -166,21 +213,27 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs) {
 #pragma unroll
   for (int c = 0; c < D; ++c)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[c][q] = scale(coef, acc[c][q]);
+    for (int q = 0; q < 4; ++q) acc(c, q) = scale(coef, acc(c, q));
   if (k.mode == HOP_SCALED && k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
 #pragma unroll
-  for (int c = 0; c < D; ++c) st_colour_ff(out, Vh, i, c, acc[c]);
+  for (int c = 0; c < D; ++c) {
+    cx<ff> v4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v4[q] = acc(c, q);
+    st_colour_ff(out, Vh, i, c, v4);
+  }
 }
 
 template <int D, bool REAL, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) hop_ff_kernel(HopK k, SkipK sk) {
+  extern __shared__ __align__(16) unsigned char ff_smem[];
   pdl_start();
   int64_t tile;
   int rhs;
   block_tile(k, tile, rhs);
   if (rhs_done(sk, rhs)) return;
   const int64_t i = tile * blockDim.x + threadIdx.x;
-  if (i < k.Vh) hop_site_ff<D, REAL>(k, i, rhs);
+  if (i < k.Vh) hop_site_ff<D, REAL>(k, i, rhs, ff_smem);
 }
 
 // Persistent multi-lattice form (the batched solver's outer residuals): every
@@ -189,12 +242,13 @@ __global__ void __launch_bounds__(MAXT, MINB) hop_ff_kernel(HopK k, SkipK sk) {
 template <int D, bool REAL>
 __global__ void __launch_bounds__(256, 1) hop_ff_multi_kernel(const HopK *descs, const int2 *items, int nitems,
                                                               const int *frozen) {
+  extern __shared__ __align__(16) unsigned char ff_smem[];
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int2 it = items[w];
     if (frozen && frozen[it.x]) continue;
     const HopK k = descs[it.x];
     const int64_t i = (int64_t)it.y * blockDim.x + threadIdx.x;
-    if (i < k.Vh) hop_site_ff<D, REAL>(k, i, 0);
+    if (i < k.Vh) hop_site_ff<D, REAL>(k, i, 0, ff_smem);
   }
 }
 
@@ -204,17 +258,33 @@ __global__ void __launch_bounds__(256, 1) hop_ff_multi_kernel(const HopK *descs,
   X(5, false, hr_ff_c5) X(6, false, hr_ff_c6) X(7, false, hr_ff_c7) X(8, false, hr_ff_c8)             \
   X(8, true, hr_ff_r8)
 
+// launch with the class's dynamic shared memory; pdl as in hop.cuh's launch_pdl
+template <typename Kern>
+static void launch_ff(Kern kern, const HopK &k, SkipK sk, dim3 grid, int bs, size_t smem, cudaStream_t st, int pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(bs);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, k, sk);
+}
+
 // register-budget variant 1 (128 threads x 3 blocks, about 168 registers)
 // only where it does not spill: d_R <= 3
 template <int D, bool REAL>
 static void launch_site_ff(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {
   if constexpr (D <= 3) {
     if (variant == 1) {
-      launch_pdl(hop_ff_kernel<D, REAL, 128, 3>, k, sk, grid, bs, st, pdl);
+      launch_ff(hop_ff_kernel<D, REAL, 128, 3>, k, sk, grid, bs, 0, st, pdl);
       return;
     }
   }
-  launch_pdl(hop_ff_kernel<D, REAL, 256, 1>, k, sk, grid, bs, st, pdl);
+  launch_ff(hop_ff_kernel<D, REAL, 256, 1>, k, sk, grid, bs, ff_smem_bytes<D, REAL>(bs), st, pdl);
 }
 
 // NAME launches the class's site kernel; NAME##_multi returns its
@@ -223,4 +293,5 @@ static void launch_site_ff(const HopK &k, SkipK sk, dim3 grid, int bs, int varia
   void NAME(const HopK &k, SkipK sk, dim3 grid, int bs, int variant, cudaStream_t st, int pdl) {   \
     launch_site_ff<DD, RE>(k, sk, grid, bs, variant, st, pdl);                                       \
   }                                                                                                  \
-  const void *NAME##_multi() { return (const void *)hop_ff_multi_kernel<DD, RE>; }
+  const void *NAME##_multi() { return (const void *)hop_ff_multi_kernel<DD, RE>; }                  \
+  size_t NAME##_smem(int bs) { return ff_smem_bytes<DD, RE>(bs); }

@@ -27,8 +27,12 @@ int hr_hop_shapes(int d, int is_real, int prec, int clover, int multi_rhs, HopSh
     // or (d_R <= 3, where it does not spill) the high budget, and the rows
     // kernel (no clover)
     if (site) {
+      // complex d_R >= 5 keeps its accumulator in shared memory (hop_ff.cuh):
+      // blocks of at most 64 threads keep that under 48 KB
       const int bss[4] = {64, 128, 32, 256};
-      for (int k = 0; k < 4; ++k) out[n++] = HopShape{0, bss[k], 0, 0};
+      const bool small_blocks = !is_real && d >= 5;
+      for (int k = 0; k < 4; ++k)
+        if (!small_blocks || bss[k] <= 64) out[n++] = HopShape{0, bss[k], 0, 0};
       if (d <= 3) {
         out[n++] = HopShape{0, 64, 1, 0};
         out[n++] = HopShape{0, 128, 1, 0};
