@@ -60,7 +60,8 @@ typedef struct hr_lattice hr_lattice;
 typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
 /* EVEN/ODD: the Schur complement Dhat on that parity; FULL: D on the whole lattice */
 typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2 } hr_parity;
-/* HR_FF: float-float, each real the unevaluated sum hi + lo of two FP32
+/* HR_FF (no counterpart in the paper, whose outer residuals are double
+ * precision, Sec. 3.3): float-float, each real the unevaluated sum hi + lo of two FP32
  * numbers (about 48 significant bits, FP32 exponent range), stored in the FP64
  * layout with each 16-byte chunk (re.hi, re.lo, im.hi, im.lo); the FP64-accurate
  * operator of the mixed solvers' outer residuals, for a part whose FP64 units
