@@ -79,6 +79,105 @@ __device__ __forceinline__ void ff_clover_inplace(const void *cl, int64_t Vh, in
   }
 }
 
+// w = B v as herm_apply does (one packed Hermitian 2d x 2d block), for even
+// d_R with the matrix cut into 4 x 4 blocks and the loops over the blocks kept
+// rolled: one copy of a diagonal block's and of an off-diagonal block's code
+// instead of every entry unrolled.  The blocks of v and w are picked by selects
+// (no run-time register indexing).  Sums run in another order than
+// herm_apply's, so results differ by rounding only.
+template <int D>
+__device__ __forceinline__ void ff_herm_blocked(const void *cl, int64_t Vh, int64_t i, int off,
+                                                const cx<ff> v[2 * D], cx<ff> w[2 * D]) {
+  constexpr int n = 2 * D, NB = n / 4;
+  static_assert(n % 4 == 0, "4 x 4 blocks");
+  auto gather = [&](const cx<ff> *x, int J, cx<ff> out[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      cx<ff> t = x[q];
+#pragma unroll
+      for (int b = 1; b < NB; ++b)
+        if (J == b) t = x[4 * b + q];
+      out[q] = t;
+    }
+  };
+  auto add_block = [&](int I, const cx<ff> d[4]) {
+    cx<ff> t[4];
+    gather(w, I, t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = t[q] + d[q];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (I == b) w[4 * b + q] = t[q];
+  };
+  auto chunk = [&](int r, int c) { return (int64_t)(off + D + r * (r - 1) / 2 + c) * Vh + i; };
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const cx<ff> dg = ld2<3>(cl, (int64_t)(off + q) * Vh + i);
+    w[2 * q] = scale(dg.x, v[2 * q]);
+    w[2 * q + 1] = scale(dg.y, v[2 * q + 1]);
+  }
+  // the strictly lower part of the diagonal blocks (I, I)
+#pragma unroll 1
+  for (int I = 0; I < NB; ++I) {
+    cx<ff> vI[4], dI[4];
+    gather(v, I, vI);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dI[q] = mk(ff(0), ff(0));
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < r; ++c) {
+        const cx<ff> a = ld2<3>(cl, chunk(4 * I + r, 4 * I + c));
+        dI[r] = cfma(a, vI[c], dI[r]);
+        dI[c] = cfmac(a, vI[r], dI[c]);
+      }
+    add_block(I, dI);
+  }
+  // the blocks (I, J) below the diagonal: w_I += B_IJ v_J, w_J += B_IJ^+ v_I
+#pragma unroll 1
+  for (int I = 1; I < NB; ++I)
+#pragma unroll 1
+    for (int J = 0; J < I; ++J) {
+      cx<ff> vI[4], vJ[4], dI[4], dJ[4];
+      gather(v, I, vI);
+      gather(v, J, vJ);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dI[q] = dJ[q] = mk(ff(0), ff(0));
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const cx<ff> a = ld2<3>(cl, chunk(4 * I + r, 4 * J + c));
+          dI[r] = cfma(a, vJ[c], dI[r]);
+          dJ[c] = cfmac(a, vI[r], dJ[c]);
+        }
+      add_block(I, dI);
+      add_block(J, dJ);
+    }
+}
+
+// The clover blocks applied in place to a shared-memory accumulator (base,
+// stride as FfAcc<D, true>): not inlined, so that the two places a launch may
+// need it share one copy of the code; even d_R uses the blocked product.
+template <int D>
+__device__ __noinline__ void ff_clover_smem(const void *cl, int64_t Vh, int64_t i, cx<ff> *base, int stride) {
+#pragma unroll 1
+  for (int b = 0; b < 2; ++b) {
+    cx<ff> v[2 * D], w[2 * D];
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[s2 * D + c] = base[(c * 4 + 2 * b + s2) * stride];
+    if constexpr (D % 2 == 0) ff_herm_blocked<D>(cl, Vh, i, b * 2 * D * D, v, w);
+    else herm_apply<D, 3>(cl, Vh, i, b * 2 * D * D, v, w);
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+      for (int c = 0; c < D; ++c) base[(c * 4 + 2 * b + s2) * stride] = w[s2 * D + c];
+  }
+}
 // smem: the block's dynamic shared memory (used when ff_smem_acc<D, REAL>())
 template <int D, bool REAL>
 __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs, unsigned char *smem) {
@@ -111,7 +210,10 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs, u
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc(c, q) = v4[q];
     }
-    if (k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
+    if (k.clover) {
+      if constexpr (SM) ff_clover_smem<D>(k.clover, Vh, i, acc.base, acc.stride);
+      else ff_clover_inplace<D>(k.clover, Vh, i, acc);
+    }
     const ff f(k.clover ? 1.0 / k.coef : k.diag / k.coef);
 #pragma unroll
     for (int c = 0; c < D; ++c)
@@ -214,7 +316,10 @@ __device__ __forceinline__ void hop_site_ff(const HopK &k, int64_t i, int rhs, u
   for (int c = 0; c < D; ++c)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc(c, q) = scale(coef, acc(c, q));
-  if (k.mode == HOP_SCALED && k.clover) ff_clover_inplace<D>(k.clover, Vh, i, acc);
+  if (k.mode == HOP_SCALED && k.clover) {
+    if constexpr (SM) ff_clover_smem<D>(k.clover, Vh, i, acc.base, acc.stride);
+    else ff_clover_inplace<D>(k.clover, Vh, i, acc);
+  }
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     cx<ff> v4[4];
