@@ -677,7 +677,7 @@ def _rel_diff(torch, lat, f_lo, prec, f64, nrhs=1):
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
-def config2(hr, inputs, torch, flush, peak):
+def bench_adj_asym_24c48(hr, inputs, torch, flush, peak):
     """SU(2) adjoint and SU(4) antisymmetric, 24^3 x 48, m0 = -0.3: Dhat GB/s per
     precision, and CG to 1e-10 (plain FP64, FP32 and FP16 inner solves)."""
     T, L, m0 = 48, 24, -0.3
@@ -712,7 +712,7 @@ def config2(hr, inputs, torch, flush, peak):
     return out
 
 
-def config3(hr, inputs, torch, flush, peak, nr=12):
+def bench_sextet_clover_12rhs(hr, inputs, torch, flush, peak, nr=12):
     """SU(3) sextet with clover (csw = 1), 32^3 x 64, m0 = -0.35, 12 right-hand
     sides: the 12-rhs Dhat (one link and clover read per site for all rhs) in
     FP32 and FP16, 12 single-rhs Dhat for comparison, and the 12-rhs CG per rhs
@@ -772,7 +772,7 @@ def config3(hr, inputs, torch, flush, peak, nr=12):
     return rec
 
 
-def config4(hr, inputs, torch, nlat=64):
+def bench_64_lattices(hr, inputs, torch, nlat=64):
     """64 lattices (8^4 ... 16^3 x 32, N = 2..6, mixed representations), m0 = -0.3:
     one batched FP32 Dhat against 64 single-lattice launches (aggregate sites/s),
     and the batched CG to 1e-8 against 64 single-lattice solves."""
@@ -836,7 +836,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-configs", action="store_true", help="skip the config 2/3/4 measurements")
+    ap.add_argument("--no-configs", action="store_true", help="skip the adjoint / antisymmetric, 12-rhs sextet and 64-lattice measurements")
     ap.add_argument("--suite", default="", help="comma list of c2,bicg,c3,c4,largen,larged,blas: measure those workloads instead")
     ap.add_argument("--shape", default="", help="pin the hop shape 'regs,G,block' (profiling runs only)")
     ap.add_argument("--prec", default="f32", choices=["f32", "f16"], help="timed Dhat precision (profiling runs only)")
@@ -1036,12 +1036,13 @@ def main():
             for k in ("mixed_fp32", "mixed_fp16", "mixed_fp32_fp64_outer", "mixed_fp16_fp64_outer"):
                 cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds"] / cg[k]["seconds"], 2)
 
-    # the other workloads (configs 2, 3, 4), inside the same clock record
+    # the other workloads (SU(2) adj / SU(4) asym 24^3x48, the 12-rhs sextet with clover,
+    # 64 small lattices), inside the same clock record; keys c2, c3, c4
     configs = None
     if not args.no_configs:
-        configs = {"c2": config2(hr, inputs, torch, flush, peaks["hbm_gbs"]),
-                   "c3": config3(hr, inputs, torch, flush, peaks["hbm_gbs"]),
-                   "c4": config4(hr, inputs, torch)}
+        configs = {"c2": bench_adj_asym_24c48(hr, inputs, torch, flush, peaks["hbm_gbs"]),
+                   "c3": bench_sextet_clover_12rhs(hr, inputs, torch, flush, peaks["hbm_gbs"]),
+                   "c4": bench_64_lattices(hr, inputs, torch)}
     clk = clocks.stop()
     traffic = ncu_traffic(f"dram_bytes_per_even_site_{args.prec}")
     roof = {"bound": "hbm", "achieved": round(gbs / world, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",

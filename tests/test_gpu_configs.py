@@ -5,12 +5,12 @@ in the neighbourhoods of the sampled sites, so the full lattices
 (32^3 x 64 and 24^3 x 48) stay affordable.  Sampled sites always include the
 lattice corners and the time boundary (where the antiperiodic sign sits).
 
-* config 1  SU(3) fund, 32^3 x 64, eps 1.0, m0 -0.4: Dhat in FP64 and FP32;
-            CG plain FP64, mixed FP32, mixed FP16 to 1e-10
-* config 2  SU(2) adj and SU(4) asym, 24^3 x 48, m0 -0.3: Dhat in FP32 and FP16;
-            mixed FP16 / FP32 CG to 1e-10
-* config 3  SU(3) sym with clover csw 1.0, 32^3 x 64, m0 -0.35, 12 rhs: Dhat on all
-            right-hand sides at once in FP32; mixed FP32 CG on all 12 to 1e-10
+* SU(3) fund, 32^3 x 64, eps 1.0, m0 -0.4: Dhat in FP64 and FP32;
+  CG plain FP64, mixed FP32, mixed FP16 to 1e-10
+* SU(2) adj and SU(4) asym, 24^3 x 48, m0 -0.3: Dhat in FP32 and FP16;
+  mixed FP16 / FP32 CG to 1e-10
+* SU(3) sym with clover csw 1.0, 32^3 x 64, m0 -0.35, 12 rhs: Dhat on all
+  right-hand sides at once in FP32; mixed FP32 CG on all 12 to 1e-10
 """
 import numpy as np
 import pytest
@@ -23,11 +23,11 @@ from paper_2405_19294_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-CONFIGS = {
-    "c1": dict(N=3, rep="fund", T=64, L=32, eps=1.0, m0=-0.4, csw=0.0, nrhs=1, precs=(0, 1, 2), inner=(0, 1, 2)),
-    "c2_adj": dict(N=2, rep="adj", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
-    "c2_asym": dict(N=4, rep="asym", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
-    "c3": dict(N=3, rep="sym", T=64, L=32, eps=1.0, m0=-0.35, csw=1.0, nrhs=12, precs=(0, 1, 2), inner=(1,)),
+WORKLOADS = {
+    "su3_fund_32c64": dict(N=3, rep="fund", T=64, L=32, eps=1.0, m0=-0.4, csw=0.0, nrhs=1, precs=(0, 1, 2), inner=(0, 1, 2)),
+    "su2_adj_24c48": dict(N=2, rep="adj", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
+    "su4_asym_24c48": dict(N=4, rep="asym", T=48, L=24, eps=1.0, m0=-0.3, csw=0.0, nrhs=1, precs=(1, 2), inner=(2, 1)),
+    "su3_sym_clover_12rhs_32c64": dict(N=3, rep="sym", T=64, L=32, eps=1.0, m0=-0.35, csw=1.0, nrhs=12, precs=(0, 1, 2), inner=(1,)),
 }
 
 _cache = {}
@@ -36,7 +36,7 @@ _cache = {}
 def _setup(hr, name):
     if name in _cache:
         return _cache[name]
-    c = CONFIGS[name]
+    c = WORKLOADS[name]
     T, L, N, rep = c["T"], c["L"], c["N"], c["rep"]
     lat = hr.Lattice(T, L, N, rep)
     a = inputs.algebra_coefficients(0, T, L, N)
@@ -78,9 +78,9 @@ def _unpack_rhs(lat, f, parity, prec, r):
     return to_complex(out)[0]
 
 
-@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("name", list(WORKLOADS))
 def test_full_size_dhat_sampled(hr, name):
-    c = CONFIGS[name]
+    c = WORKLOADS[name]
     lat, op, g, sites = _setup(hr, name)
     check_rhs = [0] if c["nrhs"] == 1 else [0, c["nrhs"] - 1]
     for prec in c["precs"]:
@@ -97,9 +97,9 @@ def test_full_size_dhat_sampled(hr, name):
         del fin, fout
 
 
-@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("name", list(WORKLOADS))
 def test_full_size_cg_to_1e10(hr, name):
-    c = CONFIGS[name]
+    c = WORKLOADS[name]
     lat, op, g, sites = _setup(hr, name)
     nrhs = c["nrhs"]
     fb_ = _load_sources(lat, c, 0, 0)
@@ -123,7 +123,7 @@ def test_full_size_cg_to_1e10(hr, name):
 
 @pytest.mark.parametrize("inner", [0, 1, 2])
 def test_cg_global_oracle_residual_16c32(hr, inner):
-    """Config 1's operator on 16^3 x 32 (V/2 = 65536 sites: hundreds of blocks per
+    """The SU(3) fund operator (eps 1.0, m0 -0.4) on 16^3 x 32 (V/2 = 65536 sites: hundreds of blocks per
     launch): the oracle's residual |b - Dhat^+ Dhat x| / |b| over the whole lattice,
     not only at sampled sites, meets the 1e-10 target the library reports."""
     from gpu_helpers import gpu_lattice, oracle_operator
@@ -148,7 +148,7 @@ def test_cg_global_oracle_residual_16c32(hr, inner):
 
 @pytest.mark.parametrize("inner", [1, 2])
 def test_multi_rhs_cg_global_oracle_residual(hr, inner):
-    """Config 3's operator (SU(3) sextet, clover csw = 1) on 8^3 x 16 with 12 right-hand
+    """The SU(3) sextet operator with clover (csw = 1, m0 -0.35) on 8^3 x 16 with 12 right-hand
     sides in one solve (FP32 or FP16 inner operator, whichever multi-rhs kernel the
     autotuner picks), checked rhs by rhs against the oracle over the whole lattice."""
     from gpu_helpers import gpu_lattice, oracle_operator
