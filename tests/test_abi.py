@@ -58,3 +58,32 @@ def test_shape_code_round_trip():
         code = hr._shape_code(shape)
         assert hr.Lattice._decode(code) == shape
     assert hr._shape_code((0, 32, 1)) == hr._shape_code((0, 32, 1, 0, 0)) == 100032
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """hr.py's ctypes mirrors of hr_info, hr_cg_params and hr_cg_stats have the size and
+    field offsets that a C compiler gives the structs of include/hr.h (a field added on
+    one side only would shift every later field)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    from paper_2405_19294_gb300 import hr
+    structs = {"hr_info": hr.hr_info, "hr_cg_params": hr.hr_cg_params, "hr_cg_stats": hr.hr_cg_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hr.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
