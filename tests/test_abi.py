@@ -87,3 +87,21 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_binding_enums_match_the_header():
+    """The precision, parity and representation codes of hr.py are the header's."""
+    from paper_2405_19294_gb300 import hr
+    txt = open(os.path.join(ROOT, "include", "hr.h")).read()
+
+    def enum(tname):
+        body = re.search(r"typedef enum \{([^}]*)\}\s*" + tname + ";", txt).group(1)
+        return {k: int(v) for k, v in re.findall(r"(HR_\w+)\s*=\s*(-?\d+)", body)}
+
+    prec = enum("hr_prec")
+    assert prec == {"HR_F64": hr.F64, "HR_F32": hr.F32, "HR_F16": hr.F16, "HR_FF": hr.FF}
+    assert sorted(hr.PREC.values()) == sorted(prec.values())
+    par = enum("hr_parity")
+    assert par == {"HR_EVEN": hr.EVEN, "HR_ODD": hr.ODD, "HR_FULL": hr.FULL}
+    rep = enum("hr_rep")
+    assert sorted(rep.values()) == sorted(hr.REP.values())
